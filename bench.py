@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark: staged 3D FFT at 512^3 FP32 on GB300 (one JSON line on stdout).
+
+Workload (the real-data full-size configuration): R2C forward then C2R
+inverse of a 512x512x512 float32 grid, real N(0,1) input (seed 2), pencil
+stages x -> y -> z in one persistent launch per transform. One step = one
+forward + one inverse. Inputs (512 MiB real, 539 MB spectrum) are larger than
+the 129 MB L2, so no flush is needed between steps.
+
+  value      GFLOP/s, 5 N log2 N per transform (the metric's convention; for a
+             real transform this is twice the 2.5 N log2 N real-flop count,
+             also reported), whole job over all ranks
+  e2e        the same metric through gbfft_exec_host on pinned HOST buffers
+             (H2D + exec + D2H inside the timed region)
+  roofline   the persistent kernel: algorithmic HBM bytes per launch / CUDA-event
+             launch time, against the measured copy bandwidth
+  cpu_baseline  the FP64 oracle on the host cores (one full step)
+
+--impl reference times the FP64 CPU oracle itself (the only reference this
+project has) on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512
+METRIC = "3D FFT GFLOP/s (5N*log2N) at 512^3 FP32, R2C fwd + C2R inv per step"
+UNIT = "GFLOP/s"
+
+
+def flops_5n(nx, ny, nz):
+    n = nx * ny * nz
+    return 5.0 * n * math.log2(n)
+
+
+def r2c_alg_bytes(nx, ny, nz):
+    """Algorithmic HBM bytes of one pencil R2C (or C2R) transform: the real
+    array once (4 B/elem), the half spectrum written by x, read+written by y
+    and z, read... i.e. 3 reads + 3 writes of the stage arrays."""
+    nc = (nx // 2 + 1) * ny * nz
+    return 4 * nx * ny * nz + 5 * 8 * nc
+
+
+def c2c_alg_bytes(nx, ny, nz, passes=3):
+    return passes * 2 * 8 * nx * ny * nz
+
+
+def slab_r2c_alg_bytes(nx, ny, nz):
+    nc = (nx // 2 + 1) * ny * nz
+    return 4 * nx * ny * nz + 3 * 8 * nc
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2601_12209_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        v = d.get("kernels", {}).get(kernel_key)
+        return float(v) if v is not None else None
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, on a bounded sample: each step is the
+    R2C forward + C2R inverse of a 256^3 grid (1/8 of the 512^3 workload)."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    n = 256
+    r = synth.normal_real((n, n, n), seed=2).numpy().astype(np.float64)
+    threads = oracle.default_threads()
+    for _ in range(args.warmup):
+        oracle.irfft3(oracle.rfft3(r, threads=threads), n, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.irfft3(oracle.rfft3(r, threads=threads), n, threads=threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2 * flops_5n(n, n, n) / dt / 1e9
+    sample = f"R2C fwd + C2R inv of a 256^3 FP64 grid per step (1/8 of the 512^3 workload), {threads} threads"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "R2C fwd + C2R inv 3D FFT, 256^3 sample of the 512^3 FP32 workload",
+                   "nx": n, "ny": n, "nz": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_oracle():
+    """One full 512^3 R2C fwd + C2R inv step of the FP64 oracle on all host cores."""
+    import numpy as np
+    import oracle
+    import synth
+    r = synth.normal_real((N, N, N), seed=2).numpy().astype(np.float64)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.irfft3(oracle.rfft3(r, threads=threads), N, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * flops_5n(N, N, N) / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one full step (512^3 R2C fwd + C2R inv, FP64) in {dt:.2f} s"}
+
+
+def time_variant(torch, plan, x, ops, steps, warmup, stream):
+    """Per-launch CUDA-event times of a list of (op, input-from) exec calls per step."""
+    bufs = {"x": x}
+    for _ in range(warmup):
+        cur = x
+        for op in ops:
+            cur = plan.exec(op, cur, stream=stream)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(ops) + 1)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for s in range(steps):
+            cur = x
+            ev[s][0].record(stream)
+            for i, op in enumerate(ops):
+                cur = plan.exec(op, cur, stream=stream)
+                ev[s][i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [[ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(steps)] for i in range(len(ops))]
+    del bufs
+    return [statistics.median(p) for p in per], [sum(p) / len(p) for p in per]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import synth
+    world, rank, local = dist_setup(args)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2601_12209_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist:
+        dist.barrier()
+    import paper_2601_12209_gb300 as gb
+    from paper_2601_12209_gb300 import abi
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    plan = gb.Plan(N, N, N, kind="r2c")
+    r = synth.normal_real((N, N, N), seed=2).to(dev)
+    spec = torch.empty((1, N, N, N // 2 + 1), dtype=torch.complex64, device=dev)
+    real_out = torch.empty((1, N, N, N), dtype=torch.float32, device=dev)
+
+    def step():
+        plan.exec(abi.GBFFT_OP_FORWARD, r, spec, stream)
+        plan.exec(abi.GBFFT_OP_INVERSE, spec, real_out, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for s in range(args.steps):
+            evs[2 * s].record(stream)
+            plan.exec(abi.GBFFT_OP_FORWARD, r, spec, stream)
+            evs[2 * s + 1].record(stream)
+            plan.exec(abi.GBFFT_OP_INVERSE, spec, real_out, stream)
+            evs[2 * s + 2].record(stream)
+        t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    fwd_ms = [evs[2 * s].elapsed_time(evs[2 * s + 1]) for s in range(args.steps)]
+    inv_ms = [evs[2 * s + 1].elapsed_time(evs[2 * s + 2]) for s in range(args.steps)]
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    flops_step = 2 * flops_5n(N, N, N)
+    value = world * flops_step / (ms_per_step * 1e-3) / 1e9
+    err = plan.device_error()
+
+    # roofline of the persistent kernel (both launches of a step are the same kernel)
+    peak, peak_kind = measured_peaks()
+    bytes_launch = r2c_alg_bytes(N, N, N)
+    avg_launch_ms = (sum(fwd_ms) + sum(inv_ms)) / (2 * args.steps)
+    achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("persistent_r2c_512")
+
+    # end to end through the C ABI on pinned host buffers
+    h_in = synth.normal_real((N, N, N), seed=2).pin_memory()
+    h_spec = torch.empty((N, N, N // 2 + 1), dtype=torch.complex64).pin_memory()
+    h_out = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    plan.exec_host(abi.GBFFT_OP_FORWARD, h_in, h_spec)
+    plan.exec_host(abi.GBFFT_OP_INVERSE, h_spec, h_out)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.exec_host(abi.GBFFT_OP_FORWARD, h_in, h_spec)
+        plan.exec_host(abi.GBFFT_OP_INVERSE, h_spec, h_out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = world * flops_step / e2e_s / 1e9
+    h2d = h_in.numel() * 4 + h_spec.numel() * 8
+    d2h = h_spec.numel() * 8 + h_out.numel() * 4
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = extra_variants(torch, gb, abi, dev, stream, max(5, args.steps // 2), 3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "R2C fwd + C2R inv 3D FFT 512x512x512 FP32, pencil, persistent launch",
+                   "nx": N, "ny": N, "nz": N, "kind": "r2c", "decomposition": "pencil",
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "1gpu",
+                   "flop_convention": "5 N log2 N per transform (real-flop count 2.5 N log2 N is half)"},
+        "gflops_real_convention": value / 2,
+        "fwd_ms": statistics.median(fwd_ms), "inv_ms": statistics.median(inv_ms),
+        "hbm_gbs_algorithmic": 2 * bytes_launch / (ms_per_step * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "persistent_kernel (R2C 512 family)", "bytes_per_launch": bytes_launch,
+                     "avg_launch_ms": avg_launch_ms, "peak_source": f"{peak_kind} hbm_gbs"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3, "path": "gbfft_exec_host (pinned host buffers)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "device_error": err,
+        "extra": extra,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        del h_in, h_spec, h_out
+        line["cpu_baseline"] = cpu_baseline_oracle()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
+    """C2C 512^3 pencil and slab, R2C slab, forward+adjoint: per-launch medians."""
+    import synth
+    out = {}
+    x = synth.uniform_complex((N, N, N), seed=3).to(dev)
+    for slab in (False, True):
+        p = gb.Plan(N, N, N, slab=slab)
+        med, avg = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+        b = c2c_alg_bytes(N, N, N, passes=2 if slab else 3)
+        key = "c2c_512_slab" if slab else "c2c_512_pencil"
+        out[key] = {"fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
+                    "gflops": 2 * flops_5n(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9,
+                    "alg_gbs": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9}
+        p.close()
+    del x
+    r = synth.normal_real((N, N, N), seed=2).to(dev)
+    p = gb.Plan(N, N, N, kind="r2c", slab=True)
+    med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+    b = slab_r2c_alg_bytes(N, N, N)
+    out["r2c_512_slab"] = {"fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
+                           "gflops": 2 * flops_5n(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9,
+                           "alg_gbs": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9}
+    p.close()
+    p = gb.Plan(N, N, N, kind="r2c")
+    med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_ADJOINT], steps, warmup, stream)
+    out["r2c_512_fwd_adjoint_ms"] = med[0] + med[1]
+    p.close()
+    ps = gb.Plan(N, N, N, kind="r2c", staged=True)
+    med, _ = time_variant(torch, ps, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+    out["r2c_512_pencil_staged_fwd_inv_ms"] = med[0] + med[1]
+    ps.close()
+    # cuFFT via torch.fft on the same GPU: context only, not a target
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        torch.fft.irfftn(torch.fft.rfftn(r), s=(N, N, N))
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        torch.fft.irfftn(torch.fft.rfftn(r), s=(N, N, N))
+    ev1.record()
+    torch.cuda.synchronize()
+    out["context_torch_fft_r2c_c2r_ms"] = ev0.elapsed_time(ev1) / steps
+    return out
+
+
+if __name__ == "__main__":
+    main()

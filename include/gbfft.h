@@ -1,0 +1,189 @@
+/*
+ * gbfft -- staged 3D FFT for one GB300 (sm_103a): C ABI.
+ *
+ * The operation (arxiv 2601.12209, Section III-A): for A of size
+ * Nx x Ny x Nz,
+ *   A^(kx,ky,kz) = sum_{i,j,l} A(i,j,l) exp(-2 pi i (kx i/Nx + ky j/Ny + kz l/Nz)),
+ * evaluated as the paper's pencil sequence: Ny*Nz length-Nx transforms, a
+ * redistribution, Nx*Nz length-Ny transforms, a redistribution, Nx*Ny
+ * length-Nz transforms (Section III-A; Algorithm 1). The slab variant
+ * (Section III-A) transforms x and y plane by plane before one redistribution
+ * and the z transforms. The inverse mirrors the sequence (Section IV-A).
+ *
+ * Layout. Arrays are row-major [batch][nz][ny][nx] (x fastest), the same
+ * element order as the paper's column-major A(i,j,l) with i = x fastest.
+ * Complex data is interleaved float32 (re, im) -- complex64. For
+ * GBFFT_R2C plans the real array is [batch][nz][ny][nx] float32 and the
+ * spectrum is [batch][nz][ny][nx/2+1] complex64 (the x axis is halved).
+ *
+ * Conventions (readings of the paper, which states no normalisation):
+ *   forward  : sign -, unscaled
+ *   inverse  : sign +, scaled by 1/(nx ny nz), so inverse(forward(x)) = x
+ *   adjoint  : conjugate transpose of forward (sign +, no scaling); for R2C,
+ *              the transpose of the real-to-complex map
+ *   inverse_adjoint : transpose of inverse (= forward / N for C2C)
+ * The C2R direction uses only the Hermitian part of the kx = 0 and kx = nx/2
+ * planes (the imaginary parts there are projected out).
+ *
+ * Ownership and memory. `in` and `out` are device pointers owned by the
+ * caller, contiguous, 16-byte aligned, and must not overlap (out-of-place;
+ * `in` is never written). The plan owns its twiddle tables, schedules and,
+ * unless gbfft_set_workspace is called, its workspace.
+ *
+ * Asynchrony. exec calls enqueue work on `stream` (a cudaStream_t, NULL =
+ * legacy default stream) and return without synchronising. Device-side
+ * errors (a dependency wait that timed out) are reported by
+ * gbfft_get_device_error. A plan may be used from one stream at a time.
+ *
+ * Errors. Every function returns 0 on success or a negative GBFFT_ERR_*
+ * code; nothing throws across this interface.
+ */
+#ifndef GBFFT_H
+#define GBFFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbfft_plan_s* gbfft_plan;
+
+/* transform kinds (Section V-B: C2C and R2C; C2R is the inverse of R2C) */
+#define GBFFT_C2C 0
+#define GBFFT_R2C 1
+
+/* arithmetic: storage is always float32 / complex64 */
+#define GBFFT_FP32 0
+
+/* plan flags */
+#define GBFFT_PENCIL 0u          /* three stages, two redistributions (Algorithm 1) */
+#define GBFFT_SLAB 1u            /* x and y per z-plane, then z (Section III-A) */
+#define GBFFT_TRANSPOSED_OUT 2u  /* pencil only: forward leaves C[b][kx][ky][kz] ("collect from C",
+                                    Algorithm 1); inverse then reads that layout */
+#define GBFFT_STAGED 4u          /* one launch per stage instead of one persistent launch */
+#define GBFFT_DEBUG_TIMEOUT (1u << 16) /* tests only: every dependency wait of the persistent launch
+                                          waits for one completion too many and times out after
+                                          ~20 ms; gbfft_get_device_error then returns
+                                          GBFFT_ERR_TIMEOUT */
+
+/* operations for gbfft_exec */
+#define GBFFT_OP_FORWARD 0
+#define GBFFT_OP_INVERSE 1
+#define GBFFT_OP_ADJOINT 2
+#define GBFFT_OP_INVERSE_ADJOINT 3
+
+/* error codes */
+#define GBFFT_OK 0
+#define GBFFT_ERR_INVALID_ARG (-1)
+#define GBFFT_ERR_UNSUPPORTED_SIZE (-2) /* a length with no kernel (see gbfft_supported_length) */
+#define GBFFT_ERR_ALIGNMENT (-3)        /* a pointer not 16-byte aligned */
+#define GBFFT_ERR_INPLACE (-4)          /* in == out */
+#define GBFFT_ERR_ALLOC (-5)            /* device allocation failed or workspace too small */
+#define GBFFT_ERR_CUDA (-6)             /* a CUDA runtime call failed */
+#define GBFFT_ERR_TIMEOUT (-7)          /* a device dependency wait ran out of time */
+#define GBFFT_ERR_NO_DEVICE (-8)        /* no CUDA device */
+
+/*
+ * Create a plan for `batch` grids of nx x ny x nz (Section V-B: a reusable
+ * plan keyed by data type, size, transform type and dimensions).
+ *   kind  : GBFFT_C2C or GBFFT_R2C (R2C needs even nx)
+ *   dtype : GBFFT_FP32
+ *   flags : GBFFT_PENCIL or GBFFT_SLAB, optionally | GBFFT_TRANSPOSED_OUT
+ *           (pencil only) | GBFFT_STAGED | GBFFT_DEBUG_TIMEOUT
+ * Every axis length (nx/2 for the R2C x axis) must satisfy
+ * gbfft_supported_length. Uses the current CUDA device; allocates twiddle
+ * tables and schedules (and the workspace lazily, on first exec).
+ * On success *out receives the plan; on failure *out is NULL.
+ */
+int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dtype, int batch,
+                      unsigned flags);
+
+/*
+ * Plan cache (Section V-B, get_or_create_plan): returns a plan shared by all
+ * callers with the same (device, nx, ny, nz, kind, dtype, batch, flags). Do
+ * not destroy it; gbfft_plan_cache_clear destroys every cached plan.
+ */
+int gbfft_plan_get_cached(gbfft_plan* out, int nx, int ny, int nz, int kind, int dtype, int batch,
+                          unsigned flags);
+void gbfft_plan_cache_clear(void);
+
+/*
+ * Run one operation (GBFFT_OP_*) from `in` to `out` on `stream`.
+ *   C2C: in/out complex64 [batch][nz][ny][nx] (TRANSPOSED_OUT: the forward
+ *        output and the inverse input are [batch][nx][ny][nz]).
+ *   R2C: FORWARD and INVERSE_ADJOINT map real -> half spectrum;
+ *        INVERSE and ADJOINT map half spectrum -> real.
+ */
+int gbfft_exec(gbfft_plan plan, int op, const void* in, void* out, void* stream);
+int gbfft_exec_forward(gbfft_plan plan, const void* in, void* out, void* stream);
+int gbfft_exec_inverse(gbfft_plan plan, const void* in, void* out, void* stream);
+int gbfft_exec_adjoint(gbfft_plan plan, const void* in, void* out, void* stream);
+int gbfft_exec_inverse_adjoint(gbfft_plan plan, const void* in, void* out, void* stream);
+
+/*
+ * Periodic Poisson solve (Section VI-B, (Periodic, Periodic, Periodic)
+ * topology): out = C2R(m * R2C(in)) / N with m(k) = -1/|k|^2, m(0) = 0, on a
+ * 2 pi-periodic box (integer wavenumbers; index j > n/2 means j - n).
+ * R2C plans only; in and out are real [batch][nz][ny][nx]. The multiplier
+ * and the inverse z transform are fused into the forward z stage. The
+ * operator is symmetric, so this call is also its own adjoint.
+ */
+int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream);
+
+/*
+ * End-to-end call on HOST buffers: copies `host_in` to the device, runs
+ * `op`, copies the result to `host_out`, and waits for completion. Uses
+ * plan-owned device buffers (allocated on first use). Pinned host memory
+ * gives asynchronous copies. op may also be 4 for gbfft_exec_poisson.
+ */
+int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out);
+
+/* Bytes of device workspace the plan needs (pencil: one or two spectrum-sized buffers). */
+int gbfft_workspace_size(gbfft_plan plan, size_t* bytes);
+/* Give the plan caller-owned workspace (>= gbfft_workspace_size bytes, 256-byte aligned). */
+int gbfft_set_workspace(gbfft_plan plan, void* dev_ptr, size_t bytes);
+
+/*
+ * Read and clear the device error word of the plan's persistent launches.
+ * Synchronises the device first. *code receives 0 or GBFFT_ERR_TIMEOUT.
+ */
+int gbfft_get_device_error(gbfft_plan plan, int* code);
+
+/*
+ * Tests only: run ONE step of the pencil pipeline with its own launch.
+ *   1 stage x forward      A[b][z][y][x]  -> B[b][z][x][y]
+ *   2 first redistribution alone (no arithmetic), same maps as step 1
+ *   3 stage y forward      B -> C[b][x][y][z]
+ *   4 second redistribution alone, same maps as step 3
+ *   5 stage z forward      C -> natural [b][z][y][x]
+ *   6 un-permute alone, same maps as step 5
+ *  11/12 stage z inverse / its map alone:  natural -> C
+ *  13/14 stage y inverse / its map alone:  C -> B
+ *  15/16 stage x inverse / its map alone:  B -> A
+ * Inverse steps apply no 1/N. Steps 2 and 16 need a C2C plan; for R2C plans
+ * the x axis of B and C has nx/2+1 bins. The redistribution-alone steps are
+ * pure moves and reproduce bit patterns exactly.
+ */
+int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* stream);
+
+/* Human-readable name of an error code (static storage). */
+const char* gbfft_strerror(int code);
+
+/* Release the plan and everything it owns. NULL is ignored. */
+void gbfft_plan_destroy(gbfft_plan plan);
+
+/* ---- host-only queries (no GPU needed) ---- */
+
+/* 1 if a pencil of length n has a compiled kernel, else 0. */
+int gbfft_supported_length(int n);
+/* Stockham radix passes used for length n: writes up to `cap` radices, returns the count (<0: unsupported). */
+int gbfft_radix_plan(int n, int* radices, int cap);
+/* Library version string. */
+const char* gbfft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFFT_H */

@@ -1,0 +1,206 @@
+"""ctypes binding of the C ABI in include/gbfft.h -- argument marshalling only.
+
+Every function keeps its C name. The library is the in-tree
+``paper_2601_12209_gb300/lib/libgbfft.so`` built by ``_build.build()``; if it
+is missing, loading raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libgbfft.so")
+
+# constants mirrored from include/gbfft.h
+GBFFT_C2C = 0
+GBFFT_R2C = 1
+GBFFT_FP32 = 0
+GBFFT_PENCIL = 0
+GBFFT_SLAB = 1
+GBFFT_TRANSPOSED_OUT = 2
+GBFFT_STAGED = 4
+GBFFT_DEBUG_TIMEOUT = 1 << 16
+GBFFT_OP_FORWARD = 0
+GBFFT_OP_INVERSE = 1
+GBFFT_OP_ADJOINT = 2
+GBFFT_OP_INVERSE_ADJOINT = 3
+GBFFT_OP_POISSON = 4  # gbfft_exec_host only
+GBFFT_OK = 0
+GBFFT_ERR_INVALID_ARG = -1
+GBFFT_ERR_UNSUPPORTED_SIZE = -2
+GBFFT_ERR_ALIGNMENT = -3
+GBFFT_ERR_INPLACE = -4
+GBFFT_ERR_ALLOC = -5
+GBFFT_ERR_CUDA = -6
+GBFFT_ERR_TIMEOUT = -7
+GBFFT_ERR_NO_DEVICE = -8
+
+# every symbol include/gbfft.h declares
+EXPORTED = (
+    "gbfft_plan_create", "gbfft_plan_get_cached", "gbfft_plan_cache_clear", "gbfft_exec",
+    "gbfft_exec_forward", "gbfft_exec_inverse", "gbfft_exec_adjoint", "gbfft_exec_inverse_adjoint",
+    "gbfft_exec_poisson", "gbfft_exec_host", "gbfft_workspace_size", "gbfft_set_workspace",
+    "gbfft_get_device_error", "gbfft_debug_run", "gbfft_strerror", "gbfft_plan_destroy",
+    "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version",
+)
+
+_lib = None
+_lock = threading.Lock()
+
+
+class GbfftError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what} failed: {strerror(code)} ({code})")
+
+
+def load() -> ctypes.CDLL:
+    """Open libgbfft.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgbfft.so is not built ({LIB_PATH}); run "
+                               "paper_2601_12209_gb300._build.build() or __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i, u, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t
+        plan_p = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "gbfft_plan_create": (i, [plan_p, i, i, i, i, i, i, u]),
+            "gbfft_plan_get_cached": (i, [plan_p, i, i, i, i, i, i, u]),
+            "gbfft_plan_cache_clear": (None, []),
+            "gbfft_exec": (i, [vp, i, vp, vp, vp]),
+            "gbfft_exec_forward": (i, [vp, vp, vp, vp]),
+            "gbfft_exec_inverse": (i, [vp, vp, vp, vp]),
+            "gbfft_exec_adjoint": (i, [vp, vp, vp, vp]),
+            "gbfft_exec_inverse_adjoint": (i, [vp, vp, vp, vp]),
+            "gbfft_exec_poisson": (i, [vp, vp, vp, vp]),
+            "gbfft_exec_host": (i, [vp, i, vp, vp]),
+            "gbfft_workspace_size": (i, [vp, ctypes.POINTER(sz)]),
+            "gbfft_set_workspace": (i, [vp, vp, sz]),
+            "gbfft_get_device_error": (i, [vp, ctypes.POINTER(i)]),
+            "gbfft_debug_run": (i, [vp, i, vp, vp, vp]),
+            "gbfft_strerror": (ctypes.c_char_p, [i]),
+            "gbfft_plan_destroy": (None, [vp]),
+            "gbfft_supported_length": (i, [i]),
+            "gbfft_radix_plan": (i, [i, ctypes.POINTER(i), i]),
+            "gbfft_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _call(name: str, *args) -> int:
+    rc = getattr(load(), name)(*args)
+    if rc != GBFFT_OK:
+        raise GbfftError(rc, name)
+    return rc
+
+
+def strerror(code: int) -> str:
+    return load().gbfft_strerror(int(code)).decode()
+
+
+def gbfft_version() -> str:
+    return load().gbfft_version().decode()
+
+
+def gbfft_supported_length(n: int) -> bool:
+    return bool(load().gbfft_supported_length(int(n)))
+
+
+def gbfft_radix_plan(n: int) -> list[int]:
+    buf = (ctypes.c_int * 16)()
+    k = load().gbfft_radix_plan(int(n), buf, 16)
+    if k < 0:
+        raise GbfftError(k, "gbfft_radix_plan")
+    return [buf[j] for j in range(k)]
+
+
+def gbfft_plan_create(nx, ny, nz, kind=GBFFT_C2C, dtype=GBFFT_FP32, batch=1, flags=0) -> int:
+    h = ctypes.c_void_p()
+    _call("gbfft_plan_create", ctypes.byref(h), int(nx), int(ny), int(nz), int(kind), int(dtype), int(batch),
+          int(flags))
+    return h.value
+
+
+def gbfft_plan_get_cached(nx, ny, nz, kind=GBFFT_C2C, dtype=GBFFT_FP32, batch=1, flags=0) -> int:
+    h = ctypes.c_void_p()
+    _call("gbfft_plan_get_cached", ctypes.byref(h), int(nx), int(ny), int(nz), int(kind), int(dtype), int(batch),
+          int(flags))
+    return h.value
+
+
+def gbfft_plan_cache_clear() -> None:
+    load().gbfft_plan_cache_clear()
+
+
+def gbfft_plan_destroy(plan: int) -> None:
+    load().gbfft_plan_destroy(ctypes.c_void_p(plan))
+
+
+def gbfft_exec(plan: int, op: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("gbfft_exec", ctypes.c_void_p(plan), int(op), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_exec_forward(plan, in_ptr, out_ptr, stream=0):
+    _call("gbfft_exec_forward", ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_exec_inverse(plan, in_ptr, out_ptr, stream=0):
+    _call("gbfft_exec_inverse", ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_exec_adjoint(plan, in_ptr, out_ptr, stream=0):
+    _call("gbfft_exec_adjoint", ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_exec_inverse_adjoint(plan, in_ptr, out_ptr, stream=0):
+    _call("gbfft_exec_inverse_adjoint", ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_exec_poisson(plan, in_ptr, out_ptr, stream=0):
+    _call("gbfft_exec_poisson", ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_exec_host(plan: int, op: int, host_in: int, host_out: int) -> None:
+    _call("gbfft_exec_host", ctypes.c_void_p(plan), int(op), ctypes.c_void_p(host_in), ctypes.c_void_p(host_out))
+
+
+def gbfft_workspace_size(plan: int) -> int:
+    n = ctypes.c_size_t()
+    _call("gbfft_workspace_size", ctypes.c_void_p(plan), ctypes.byref(n))
+    return n.value
+
+
+def gbfft_set_workspace(plan: int, ptr: int, nbytes: int) -> None:
+    _call("gbfft_set_workspace", ctypes.c_void_p(plan), ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes))
+
+
+def gbfft_get_device_error(plan: int) -> int:
+    c = ctypes.c_int()
+    _call("gbfft_get_device_error", ctypes.c_void_p(plan), ctypes.byref(c))
+    return c.value
+
+
+def gbfft_debug_run(plan: int, step: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("gbfft_debug_run", ctypes.c_void_p(plan), int(step), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def raw_rc(name: str, *args) -> int:
+    """Call a C function and return its code without raising (for error-path tests)."""
+    return getattr(load(), name)(*args)

@@ -1,0 +1,904 @@
+// Host side of the C ABI declared in include/gbfft.h: plans, stage
+// descriptors of the pencil and slab pipelines, persistent schedules, kernel
+// dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gbfft.h"
+#include "gbfft_kernels.cuh"
+
+namespace gbfft {
+
+void register_stage_group_0(std::vector<StageKernel>&);
+void register_stage_group_1(std::vector<StageKernel>&);
+void register_stage_group_2(std::vector<StageKernel>&);
+void register_stage_group_3(std::vector<StageKernel>&);
+void register_stage_group_4(std::vector<StageKernel>&);
+void register_stage_group_5(std::vector<StageKernel>&);
+void register_stage_group_6(std::vector<StageKernel>&);
+void register_stage_group_7(std::vector<StageKernel>&);
+void register_persistent_group_0(std::vector<PersistentKernel>&);
+void register_persistent_group_1(std::vector<PersistentKernel>&);
+
+std::vector<StageKernel>& stage_registry() {
+  static std::vector<StageKernel> v;
+  return v;
+}
+std::vector<PersistentKernel>& persistent_registry() {
+  static std::vector<PersistentKernel> v;
+  return v;
+}
+
+static std::once_flag g_reg_once;
+static void ensure_registry() {
+  std::call_once(g_reg_once, [] {
+    auto& s = stage_registry();
+    register_stage_group_0(s);
+    register_stage_group_1(s);
+    register_stage_group_2(s);
+    register_stage_group_3(s);
+    register_stage_group_4(s);
+    register_stage_group_5(s);
+    register_stage_group_6(s);
+    register_stage_group_7(s);
+    auto& p = persistent_registry();
+    register_persistent_group_0(p);
+    register_persistent_group_1(p);
+  });
+}
+
+// Host-side mirror of make_radices (device code is not callable here at
+// run time for a runtime n).
+static int host_radices(int n, int* out, int cap) {
+  if (n < 2) return -1;
+  int m = n, a = 0, cnt = 0;
+  int tmp[16];
+  while (m % 2 == 0) {
+    ++a;
+    m /= 2;
+  }
+  if (a > 0) {
+    int passes = (a + 3) / 4;
+    int base = a / passes, extra = a % passes;
+    for (int i = 0; i < passes; ++i) tmp[cnt++] = 1 << (base + (i < extra ? 1 : 0));
+  }
+  while (m % 3 == 0) {
+    tmp[cnt++] = 3;
+    m /= 3;
+  }
+  while (m % 5 == 0) {
+    tmp[cnt++] = 5;
+    m /= 5;
+  }
+  if (m != 1) return -1;
+  for (int i = 0; i < cnt && i < cap; ++i) out[i] = tmp[i];
+  return cnt;
+}
+
+static const StageKernel* find_stage(int L, int dir, int kind) {
+  ensure_registry();
+  for (const auto& k : stage_registry())
+    if (k.L == L && k.dir == dir && k.kind == kind) return &k;
+  return nullptr;
+}
+
+static bool stage_supported(int L) { return find_stage(L, -1, kPlain) != nullptr; }
+
+// Per-device launch facts of one kernel (max dynamic smem set, blocks per SM).
+struct LaunchInfo {
+  int blocks_per_sm = 0;
+  bool ready = false;
+};
+static std::mutex g_launch_mu;
+static std::map<std::tuple<int, const void*, size_t>, LaunchInfo> g_launch;
+
+static cudaError_t launch_info(const void* fn, int threads, size_t smem, int* blocks_per_sm) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  LaunchInfo& li = g_launch[std::make_tuple(dev, fn, smem)];
+  if (!li.ready) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    li.blocks_per_sm = std::max(nb, 1);
+    li.ready = true;
+  }
+  *blocks_per_sm = li.blocks_per_sm;
+  return cudaSuccess;
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return std::max(n, 1);
+}
+
+}  // namespace gbfft
+
+using namespace gbfft;
+
+// ----------------------------------------------------------------- the plan
+
+enum Pipe { kPipeFwd = 0, kPipeInv = 1, kPipePoisson = 2, kNumPipes = 3 };
+
+struct gbfft_plan_s {
+  int nx, ny, nz, batch, kind, dtype;
+  unsigned flags;
+  int device;
+  int nxc, Lx, rowA;  // spectrum x bins, x transform length, complex per input row
+  long long Nc, NA;   // spectrum / input float2 elements per batch entry
+  // twiddle tables (device)
+  float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr, *tw2 = nullptr;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  int n_ws = 0;
+  // persistent launch state
+  Control* ctl = nullptr;
+  unsigned int* counters = nullptr;
+  size_t counters_words = 0;
+  unsigned int* sched[kNumPipes] = {nullptr, nullptr, nullptr};
+  unsigned int sched_len[kNumPipes] = {0, 0, 0};
+  // end-to-end host path
+  void* h_in_dev = nullptr;
+  void* h_out_dev = nullptr;
+  size_t h_in_bytes = 0, h_out_bytes = 0;
+  cudaStream_t h_stream = nullptr;
+};
+
+static int cuda_err(cudaError_t e) { return e == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA; }
+
+static bool is_r2c(const gbfft_plan_s* p) { return p->kind == GBFFT_R2C; }
+static bool is_slab(const gbfft_plan_s* p) { return (p->flags & GBFFT_SLAB) != 0; }
+
+static int gchunks(int n) { return (n + kTileP - 1) / kTileP; }
+
+static StageDesc mk(const void* in, void* out, int L, int kind, int dir, int batch, int n_outer, int n_group,
+                    long long ib, long long io, long long ig, long long in_, int im, long long ob, long long oo,
+                    long long og, long long on_, int om, float scale, float interior, const float2* tw,
+                    const float2* tw2) {
+  StageDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.in = reinterpret_cast<const float2*>(in);
+  d.out = reinterpret_cast<float2*>(out);
+  d.in_b = ib;
+  d.in_o = io;
+  d.in_g = ig;
+  d.in_n = in_;
+  d.out_b = ob;
+  d.out_o = oo;
+  d.out_g = og;
+  d.out_n = on_;
+  d.batch = batch;
+  d.n_outer = n_outer;
+  d.n_group = n_group;
+  d.n_gchunks = gchunks(n_group);
+  d.n_tiles = (long long)batch * n_outer * d.n_gchunks;
+  d.L = L;
+  d.n_in = kind == kC2RPre ? L + 1 : L;
+  d.n_out = kind == kR2CPost ? L + 1 : L;
+  d.in_mode = im;
+  d.out_mode = om;
+  d.kind = kind;
+  d.dir = dir;
+  d.scale = scale;
+  d.interior = interior;
+  d.tw = tw;
+  d.tw2 = tw2;
+  d.dep_rule = kDepNone;
+  return d;
+}
+
+static void dep(StageDesc& d, int rule, const StageDesc& prev) {
+  d.dep_rule = rule;
+  d.prev_n_outer = prev.n_outer;
+  d.prev_n_gchunks = prev.n_gchunks;
+}
+
+// Tile order of a stage inside a persistent schedule.
+enum TileOrder { kOrderNatural = 0, kOrderGchunkMajor = 1 };
+
+struct Pipeline {
+  StageDesc st[kMaxStages];
+  int order[kMaxStages];
+  long long in_cap[kMaxStages];   // float2 capacity of the buffer each stage reads
+  long long out_cap[kMaxStages];  // ... and writes (-1: unknown, not checked)
+  int n = 0;
+};
+
+// A buffer of the pipeline and its capacity in float2 elements.
+struct Buf {
+  void* p;
+  long long cap;
+};
+
+// Largest float2 offset + 1 a stage reads / writes (all strides are positive).
+static long long read_extent(const StageDesc& d) {
+  return (long long)(d.batch - 1) * d.in_b + (long long)(d.n_outer - 1) * d.in_o +
+         (long long)(d.n_group - 1) * d.in_g + (long long)(d.n_in - 1) * d.in_n + 1;
+}
+static long long write_extent(const StageDesc& d) {
+  return (long long)(d.batch - 1) * d.out_b + (long long)(d.n_outer - 1) * d.out_o +
+         (long long)(d.n_group - 1) * d.out_g + (long long)(d.n_out - 1) * d.out_n + 1;
+}
+
+// Stage descriptors of one operation. Buffers: in, out, W1, W2 (workspace).
+// Layouts (float2 units; nxc = spectrum x bins):
+//   A natural input  [b][z][y][rowA]   B [b][z][kx][y]   C [b][kx][y][z]
+//   S natural spectrum [b][z][y][kx]
+static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin, Buf bout, Buf b1, Buf b2) {
+  Pipeline P;
+  const void* in = bin.p;
+  void* out = bout.p;
+  void* W1 = b1.p;
+  void* W2 = b2.p;
+  // capacity of whichever buffer a stage uses (matched by role, not address)
+  auto cap_of = [&](int role) -> long long {
+    switch (role) {
+      case 0: return bin.cap;
+      case 1: return bout.cap;
+      case 2: return b1.cap;
+      default: return b2.cap;
+    }
+  };
+  const int B = p->batch, nx = p->nx, ny = p->ny, nz = p->nz, nxc = p->nxc, Lx = p->Lx, rowA = p->rowA;
+  const long long Nc = p->Nc, NA = p->NA;
+  const bool r2c = is_r2c(p);
+  const float invN = (float)(1.0 / ((double)nx * (double)ny * (double)nz));
+  const int kx_kind_f = r2c ? kR2CPost : kPlain;
+  const int kx_kind_i = r2c ? kC2RPre : kPlain;
+  // roles: 0 in, 1 out, 2 W1, 3 W2
+  auto add = [&](const StageDesc& d, int order, int rin, int rout) {
+    P.st[P.n] = d;
+    P.order[P.n] = order;
+    P.in_cap[P.n] = cap_of(rin);
+    P.out_cap[P.n] = cap_of(rout);
+    ++P.n;
+  };
+  if (pipe == kPipeFwd) {
+    const float interior = (op == GBFFT_OP_INVERSE_ADJOINT) ? 2.f : 1.f;
+    const float scale = (op == GBFFT_OP_INVERSE_ADJOINT) ? invN : 1.f;
+    if (!is_slab(p)) {
+      StageDesc X = mk(in, out, Lx, kx_kind_f, -1, B, nz, ny, NA, (long long)rowA * ny, rowA, 1, kRow, Nc,
+                       (long long)nxc * ny, 1, ny, kCol, 1.f, r2c ? interior : 1.f, p->tw_x, p->tw2);
+      StageDesc Y = mk(out, W1, ny, kPlain, -1, B, nxc, nz, Nc, ny, (long long)nxc * ny, 1, kRow, Nc,
+                       (long long)ny * nz, 1, nz, kCol, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Y, kDepGroup, X);
+      StageDesc Z;
+      if (p->flags & GBFFT_TRANSPOSED_OUT)
+        Z = mk(W1, out, nz, kPlain, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nz,
+               (long long)ny * nz, 1, kRow, scale, 1.f, p->tw_z, nullptr);
+      else
+        Z = mk(W1, out, nz, kPlain, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nxc, 1,
+               (long long)nxc * ny, kCol, scale, 1.f, p->tw_z, nullptr);
+      dep(Z, kDepGroup, Y);
+      add(X, kOrderNatural, 0, 1);
+      add(Y, kOrderGchunkMajor, 1, 2);
+      add(Z, kOrderNatural, 2, 1);
+    } else {
+      StageDesc X = mk(in, out, Lx, kx_kind_f, -1, B, nz, ny, NA, (long long)rowA * ny, rowA, 1, kRow, Nc,
+                       (long long)nxc * ny, nxc, 1, kRow, 1.f, r2c ? interior : 1.f, p->tw_x, p->tw2);
+      StageDesc Y = mk(out, out, ny, kPlain, -1, B, nz, nxc, Nc, (long long)nxc * ny, 1, nxc, kCol, Nc,
+                       (long long)nxc * ny, 1, nxc, kCol, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Y, kDepOuter, X);
+      StageDesc Z = mk(out, out, nz, kPlain, -1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nxc, 1,
+                       (long long)nxc * ny, kCol, scale, 1.f, p->tw_z, nullptr);
+      dep(Z, kDepSameGchunk, Y);
+      add(X, kOrderNatural, 0, 1);
+      add(Y, kOrderNatural, 1, 1);
+      add(Z, kOrderNatural, 1, 1);
+    }
+  } else if (pipe == kPipeInv) {
+    const float interior = (op == GBFFT_OP_ADJOINT) ? 0.5f : 1.f;
+    const float scale = (op == GBFFT_OP_INVERSE) ? invN : 1.f;
+    if (!is_slab(p)) {
+      void* Cb = r2c ? W1 : out;
+      void* Bb = r2c ? W2 : W1;
+      StageDesc Z;
+      if (p->flags & GBFFT_TRANSPOSED_OUT)
+        Z = mk(in, Cb, nz, kPlain, +1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nz,
+               (long long)ny * nz, 1, kRow, 1.f, 1.f, p->tw_z, nullptr);
+      else
+        Z = mk(in, Cb, nz, kPlain, +1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nz,
+               (long long)ny * nz, 1, kRow, 1.f, 1.f, p->tw_z, nullptr);
+      StageDesc Y = mk(Cb, Bb, ny, kPlain, +1, B, nxc, nz, Nc, (long long)ny * nz, 1, nz, kCol, Nc, ny,
+                       (long long)nxc * ny, 1, kRow, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Y, kDepGchunkOfOuter, Z);
+      StageDesc X = mk(Bb, out, Lx, kx_kind_i, +1, B, nz, ny, Nc, (long long)nxc * ny, 1, ny, kCol, NA,
+                       (long long)rowA * ny, rowA, 1, kRow, scale, r2c ? interior : 1.f, p->tw_x, p->tw2);
+      dep(X, kDepGchunkOfOuter, Y);
+      add(Z, kOrderNatural, 0, r2c ? 2 : 1);
+      add(Y, kOrderGchunkMajor, r2c ? 2 : 1, r2c ? 3 : 2);
+      add(X, kOrderNatural, r2c ? 3 : 2, 1);
+    } else {
+      void* D = r2c ? W1 : out;
+      StageDesc Z = mk(in, D, nz, kPlain, +1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nxc, 1,
+                       (long long)nxc * ny, kCol, 1.f, 1.f, p->tw_z, nullptr);
+      StageDesc Y = mk(D, D, ny, kPlain, +1, B, nz, nxc, Nc, (long long)nxc * ny, 1, nxc, kCol, Nc,
+                       (long long)nxc * ny, 1, nxc, kCol, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Y, kDepSameGchunk, Z);
+      StageDesc X = mk(D, out, Lx, kx_kind_i, +1, B, nz, ny, Nc, (long long)nxc * ny, nxc, 1, kRow, NA,
+                       (long long)rowA * ny, rowA, 1, kRow, scale, r2c ? interior : 1.f, p->tw_x, p->tw2);
+      dep(X, kDepOuter, Y);
+      add(Z, kOrderGchunkMajor, 0, r2c ? 2 : 1);
+      add(Y, kOrderNatural, r2c ? 2 : 1, r2c ? 2 : 1);
+      add(X, kOrderNatural, r2c ? 2 : 1, 1);
+    }
+  } else {  // Poisson (R2C plans)
+    const int M = Lx;
+    if (!is_slab(p)) {
+      StageDesc X = mk(in, W1, M, kR2CPost, -1, B, nz, ny, NA, (long long)M * ny, M, 1, kRow, Nc,
+                       (long long)nxc * ny, 1, ny, kCol, 1.f, 1.f, p->tw_x, p->tw2);
+      StageDesc Y = mk(W1, W2, ny, kPlain, -1, B, nxc, nz, Nc, ny, (long long)nxc * ny, 1, kRow, Nc,
+                       (long long)ny * nz, 1, nz, kCol, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Y, kDepGroup, X);
+      StageDesc PZ = mk(W2, W2, nz, kPoissonZ, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nz,
+                        (long long)ny * nz, 1, kRow, invN, 1.f, p->tw_z, nullptr);
+      PZ.pz_nx = nx;
+      PZ.pz_ny = ny;
+      dep(PZ, kDepGroup, Y);
+      StageDesc Yi = mk(W2, W1, ny, kPlain, +1, B, nxc, nz, Nc, (long long)ny * nz, 1, nz, kCol, Nc, ny,
+                        (long long)nxc * ny, 1, kRow, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Yi, kDepGchunkOfOuter, PZ);
+      StageDesc Xi = mk(W1, out, M, kC2RPre, +1, B, nz, ny, Nc, (long long)nxc * ny, 1, ny, kCol, NA,
+                        (long long)M * ny, M, 1, kRow, 1.f, 1.f, p->tw_x, p->tw2);
+      dep(Xi, kDepGchunkOfOuter, Yi);
+      add(X, kOrderNatural, 0, 2);
+      add(Y, kOrderGchunkMajor, 2, 3);
+      add(PZ, kOrderNatural, 3, 3);
+      add(Yi, kOrderGchunkMajor, 3, 2);
+      add(Xi, kOrderNatural, 2, 1);
+    } else {
+      StageDesc X = mk(in, W1, M, kR2CPost, -1, B, nz, ny, NA, (long long)M * ny, M, 1, kRow, Nc,
+                       (long long)nxc * ny, nxc, 1, kRow, 1.f, 1.f, p->tw_x, p->tw2);
+      StageDesc Y = mk(W1, W1, ny, kPlain, -1, B, nz, nxc, Nc, (long long)nxc * ny, 1, nxc, kCol, Nc,
+                       (long long)nxc * ny, 1, nxc, kCol, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Y, kDepOuter, X);
+      StageDesc PZ = mk(W1, W1, nz, kPoissonZ, -1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nxc,
+                        1, (long long)nxc * ny, kCol, invN, 1.f, p->tw_z, nullptr);
+      PZ.pz_nx = nx;
+      PZ.pz_ny = ny;
+      dep(PZ, kDepSameGchunk, Y);
+      StageDesc Yi = mk(W1, W1, ny, kPlain, +1, B, nz, nxc, Nc, (long long)nxc * ny, 1, nxc, kCol, Nc,
+                        (long long)nxc * ny, 1, nxc, kCol, 1.f, 1.f, p->tw_y, nullptr);
+      dep(Yi, kDepSameGchunk, PZ);
+      StageDesc Xi = mk(W1, out, M, kC2RPre, +1, B, nz, ny, Nc, (long long)nxc * ny, nxc, 1, kRow, NA,
+                        (long long)M * ny, M, 1, kRow, 1.f, 1.f, p->tw_x, p->tw2);
+      dep(Xi, kDepOuter, Yi);
+      add(X, kOrderNatural, 0, 2);
+      add(Y, kOrderNatural, 2, 2);
+      add(PZ, kOrderGchunkMajor, 2, 2);
+      add(Yi, kOrderNatural, 2, 2);
+      add(Xi, kOrderNatural, 2, 1);
+    }
+  }
+  return P;
+}
+
+static int pipe_of(int op) {
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT) return kPipeFwd;
+  if (op == GBFFT_OP_INVERSE || op == GBFFT_OP_ADJOINT) return kPipeInv;
+  return kPipePoisson;
+}
+
+// Ticket list of a persistent launch: stage by stage, each stage's tiles in
+// the order that lets it start as early as its dependency rule allows.
+static std::vector<unsigned int> build_schedule(const Pipeline& P) {
+  std::vector<unsigned int> s;
+  for (int k = 0; k < P.n; ++k) {
+    const StageDesc& d = P.st[k];
+    const unsigned int tag = (unsigned int)k << 28;
+    if (P.order[k] == kOrderNatural) {
+      for (long long t = 0; t < d.n_tiles; ++t) s.push_back(tag | (unsigned int)t);
+    } else {
+      for (int b = 0; b < d.batch; ++b)
+        for (int gc = 0; gc < d.n_gchunks; ++gc)
+          for (int o = 0; o < d.n_outer; ++o)
+            s.push_back(tag | (unsigned int)(((long long)b * d.n_outer + o) * d.n_gchunks + gc));
+    }
+  }
+  return s;
+}
+
+static size_t counter_words(const Pipeline& P) {
+  size_t w = 0;
+  for (int k = 0; k < P.n; ++k) {
+    const StageDesc& d = P.st[k];
+    w += (size_t)d.batch * d.n_outer + (size_t)d.batch * d.n_gchunks + (size_t)d.batch;
+  }
+  return w;
+}
+
+static const PersistentKernel* find_persistent(const Pipeline& P) {
+  ensure_registry();
+  for (const auto& k : persistent_registry()) {
+    bool all = true;
+    for (int s = 0; s < P.n && all; ++s) {
+      const int code = kcode(P.st[s].L, P.st[s].kind, P.st[s].dir);
+      bool found = false;
+      for (int i = 0; i < k.ncodes; ++i) found |= (k.codes[i] == code);
+      all = found;
+    }
+    if (all) return &k;
+  }
+  return nullptr;
+}
+
+static int launch_stage(const StageDesc& d, cudaStream_t stream) {
+  if (d.n_tiles == 0) return GBFFT_OK;
+  const StageKernel* k = find_stage(d.L, d.dir, d.kind);
+  if (!k) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  int bpsm = 1;
+  cudaError_t e = launch_info(k->fn, k->threads, k->smem, &bpsm);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
+  StageDesc dd = d;
+  void* args[] = {&dd};
+  e = cudaLaunchKernel(k->fn, dim3((unsigned)grid), dim3((unsigned)k->threads), args, k->smem, stream);
+  return cuda_err(e);
+}
+
+static int ensure_workspace(gbfft_plan_s* p) {
+  if (p->n_ws == 0 || p->ws) return GBFFT_OK;
+  size_t need = 0;
+  gbfft_workspace_size(p, &need);
+  if (cudaMalloc(&p->ws, need) != cudaSuccess) {
+    p->ws = nullptr;
+    cudaGetLastError();
+    return GBFFT_ERR_ALLOC;
+  }
+  p->ws_bytes = need;
+  p->ws_owned = true;
+  return GBFFT_OK;
+}
+
+static size_t spectrum_bytes(const gbfft_plan_s* p) {
+  size_t b = (size_t)p->Nc * (size_t)p->batch * sizeof(float2);
+  return (b + 255) & ~(size_t)255;
+}
+
+// Host-side bounds check of every stage against the buffers it touches: an
+// indexing error becomes GBFFT_ERR_INVALID_ARG instead of a launch.
+static int validate(const Pipeline& P) {
+  for (int s = 0; s < P.n; ++s) {
+    const StageDesc& d = P.st[s];
+    if (d.n_tiles <= 0 || d.batch < 1 || d.n_outer < 1 || d.n_group < 1) return GBFFT_ERR_INVALID_ARG;
+    if (d.in_mode == kRow ? d.in_n != 1 : d.in_g != 1) return GBFFT_ERR_INVALID_ARG;
+    if (d.out_mode == kRow ? d.out_n != 1 : d.out_g != 1) return GBFFT_ERR_INVALID_ARG;
+    if (P.in_cap[s] >= 0 && read_extent(d) > P.in_cap[s]) return GBFFT_ERR_INVALID_ARG;
+    if (P.out_cap[s] >= 0 && write_extent(d) > P.out_cap[s]) return GBFFT_ERR_INVALID_ARG;
+    if (!d.in || !d.out || !d.tw) return GBFFT_ERR_INVALID_ARG;
+    if ((d.kind == kR2CPost || d.kind == kC2RPre) && !d.tw2) return GBFFT_ERR_INVALID_ARG;
+  }
+  return GBFFT_OK;
+}
+
+static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream_t stream) {
+  int vrc = validate(P);
+  if (vrc) return vrc;
+  const bool staged = (p->flags & GBFFT_STAGED) != 0;
+  const PersistentKernel* pk = staged ? nullptr : find_persistent(P);
+  if (!pk) {
+    for (int s = 0; s < P.n; ++s) {
+      int rc = launch_stage(P.st[s], stream);
+      if (rc) return rc;
+    }
+    return GBFFT_OK;
+  }
+  PersistentArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nstages = P.n;
+  for (int s = 0; s < P.n; ++s) a.st[s] = P.st[s];
+  a.sched = p->sched[pipe];
+  a.total = p->sched_len[pipe];
+  a.ctl = p->ctl;
+  unsigned int* c = p->counters;
+  for (int s = 0; s < P.n; ++s) {
+    const StageDesc& d = P.st[s];
+    a.cnt_outer[s] = c;
+    c += (size_t)d.batch * d.n_outer;
+    a.cnt_gchunk[s] = c;
+    c += (size_t)d.batch * d.n_gchunks;
+    a.cnt_total[s] = c;
+    c += (size_t)d.batch;
+  }
+  const bool dbg = (p->flags & GBFFT_DEBUG_TIMEOUT) != 0;
+  a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
+  a.debug_never = dbg ? 1 : 0;
+  cudaError_t e = cudaMemsetAsync(p->ctl, 0, sizeof(Control) + p->counters_words * sizeof(unsigned int), stream);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  const size_t smem = pk->smem + (size_t)P.n * pk->tw_smem_per_stage;
+  int bpsm = 1;
+  e = launch_info(pk->fn, pk->threads, smem, &bpsm);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  long long grid = std::min<long long>((long long)a.total, (long long)sm_count() * bpsm);
+  void* args[] = {&a};
+  e = cudaLaunchKernel(pk->fn, dim3((unsigned)std::max<long long>(grid, 1)), dim3((unsigned)pk->threads), args,
+                       smem, stream);
+  return cuda_err(e);
+}
+
+static float2* upload_table(const std::vector<float2>& h) {
+  float2* d = nullptr;
+  if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  return d;
+}
+
+// W_n^t = exp(-2 pi i t / n) for t in [0, count), computed in FP64 and rounded once.
+static std::vector<float2> twiddle_table(int n, int count) {
+  std::vector<float2> h((size_t)count);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int t = 0; t < count; ++t) {
+    double a = two_pi * (double)(t % n) / (double)n;
+    h[(size_t)t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  return h;
+}
+
+static void free_plan(gbfft_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->tw_x);
+  cudaFree(p->tw_y);
+  cudaFree(p->tw_z);
+  cudaFree(p->tw2);
+  if (p->ws_owned) cudaFree(p->ws);
+  cudaFree(p->ctl);
+  for (int i = 0; i < kNumPipes; ++i) cudaFree(p->sched[i]);
+  cudaFree(p->h_in_dev);
+  cudaFree(p->h_out_dev);
+  if (p->h_stream) cudaStreamDestroy(p->h_stream);
+  delete p;
+}
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* gbfft_version(void) { return "gbfft 0.1 (sm_103a)"; }
+
+const char* gbfft_strerror(int code) {
+  switch (code) {
+    case GBFFT_OK:
+      return "ok";
+    case GBFFT_ERR_INVALID_ARG:
+      return "invalid argument";
+    case GBFFT_ERR_UNSUPPORTED_SIZE:
+      return "unsupported transform length";
+    case GBFFT_ERR_ALIGNMENT:
+      return "pointer not 16-byte aligned";
+    case GBFFT_ERR_INPLACE:
+      return "in-place execution is not supported (in == out)";
+    case GBFFT_ERR_ALLOC:
+      return "device allocation failed or workspace too small";
+    case GBFFT_ERR_CUDA:
+      return "CUDA runtime error";
+    case GBFFT_ERR_TIMEOUT:
+      return "device dependency wait timed out";
+    case GBFFT_ERR_NO_DEVICE:
+      return "no CUDA device";
+    default:
+      return "unknown error";
+  }
+}
+
+int gbfft_radix_plan(int n, int* radices, int cap) {
+  if (!radices || cap < 0) return GBFFT_ERR_INVALID_ARG;
+  int r = host_radices(n, radices, cap);
+  return r < 0 ? GBFFT_ERR_UNSUPPORTED_SIZE : r;
+}
+
+int gbfft_supported_length(int n) { return (n >= 2 && stage_supported(n)) ? 1 : 0; }
+
+int gbfft_workspace_size(gbfft_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return GBFFT_ERR_INVALID_ARG;
+  *bytes = (size_t)plan->n_ws * spectrum_bytes(plan);
+  return GBFFT_OK;
+}
+
+int gbfft_set_workspace(gbfft_plan plan, void* dev_ptr, size_t bytes) {
+  if (!plan) return GBFFT_ERR_INVALID_ARG;
+  size_t need = 0;
+  gbfft_workspace_size(plan, &need);
+  if (need == 0) return GBFFT_OK;
+  if (!dev_ptr) return GBFFT_ERR_INVALID_ARG;
+  if (((uintptr_t)dev_ptr) % 256 != 0) return GBFFT_ERR_ALIGNMENT;
+  if (bytes < need) return GBFFT_ERR_ALLOC;
+  if (plan->ws_owned) cudaFree(plan->ws);
+  plan->ws = dev_ptr;
+  plan->ws_bytes = bytes;
+  plan->ws_owned = false;
+  return GBFFT_OK;
+}
+
+int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dtype, int batch, unsigned flags) {
+  if (!out) return GBFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nz < 2 || batch < 1) return GBFFT_ERR_INVALID_ARG;
+  if (kind != GBFFT_C2C && kind != GBFFT_R2C) return GBFFT_ERR_INVALID_ARG;
+  if (dtype != GBFFT_FP32) return GBFFT_ERR_INVALID_ARG;
+  const unsigned known = GBFFT_SLAB | GBFFT_TRANSPOSED_OUT | GBFFT_STAGED | GBFFT_DEBUG_TIMEOUT;
+  if (flags & ~known) return GBFFT_ERR_INVALID_ARG;
+  if ((flags & GBFFT_SLAB) && (flags & GBFFT_TRANSPOSED_OUT)) return GBFFT_ERR_INVALID_ARG;
+  if (kind == GBFFT_R2C && (nx % 2 != 0 || nx < 4)) return GBFFT_ERR_INVALID_ARG;
+  const int Lx = kind == GBFFT_R2C ? nx / 2 : nx;
+  if (!stage_supported(Lx) || !stage_supported(ny) || !stage_supported(nz)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  if (kind == GBFFT_R2C && (!find_stage(Lx, -1, kR2CPost) || !find_stage(Lx, 1, kC2RPre)))
+    return GBFFT_ERR_UNSUPPORTED_SIZE;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return GBFFT_ERR_NO_DEVICE;
+  }
+  gbfft_plan_s* p = new gbfft_plan_s();
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->batch = batch;
+  p->kind = kind;
+  p->dtype = dtype;
+  p->flags = flags;
+  cudaGetDevice(&p->device);
+  p->nxc = kind == GBFFT_R2C ? nx / 2 + 1 : nx;
+  p->Lx = Lx;
+  p->rowA = Lx;  // complex values per input row (real pairs for R2C)
+  p->Nc = (long long)p->nxc * ny * nz;
+  p->NA = (long long)p->rowA * ny * nz;
+  // tiles are indexed with 28 bits in the persistent schedule
+  if ((long long)batch * std::max<long long>((long long)nz * gchunks(ny),
+                                             std::max<long long>((long long)p->nxc * gchunks(nz),
+                                                                 (long long)ny * gchunks(p->nxc))) >=
+      (1LL << 28)) {
+    delete p;
+    return GBFFT_ERR_INVALID_ARG;
+  }
+  // workspace buffers: pencil C2C 1; pencil R2C 2 (inverse, Poisson); slab R2C 1; slab C2C 0
+  if (!is_slab(p))
+    p->n_ws = kind == GBFFT_R2C ? 2 : 1;
+  else
+    p->n_ws = kind == GBFFT_R2C ? 1 : 0;
+
+  p->tw_x = upload_table(twiddle_table(Lx, Lx));
+  p->tw_y = upload_table(twiddle_table(ny, ny));
+  p->tw_z = upload_table(twiddle_table(nz, nz));
+  bool ok = p->tw_x && p->tw_y && p->tw_z;
+  if (ok && kind == GBFFT_R2C) {
+    p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
+    ok = p->tw2 != nullptr;
+  }
+  // persistent schedules and counters
+  size_t words = 0;
+  for (int pipe = 0; pipe < kNumPipes && ok; ++pipe) {
+    if (pipe == kPipePoisson && kind != GBFFT_R2C) continue;
+    int op = pipe == kPipeFwd ? GBFFT_OP_FORWARD : (pipe == kPipeInv ? GBFFT_OP_INVERSE : 4);
+    const Buf none{nullptr, -1};
+    Pipeline P = build_pipeline(p, pipe, op, none, none, none, none);
+    std::vector<unsigned int> s = build_schedule(P);
+    words = std::max(words, counter_words(P));
+    if (cudaMalloc(&p->sched[pipe], s.size() * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemcpy(p->sched[pipe], s.data(), s.size() * sizeof(unsigned int), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      ok = false;
+      break;
+    }
+    p->sched_len[pipe] = (unsigned int)s.size();
+  }
+  if (ok) {
+    p->counters_words = words;
+    void* c = nullptr;
+    if (cudaMalloc(&c, sizeof(Control) + words * sizeof(unsigned int)) != cudaSuccess) {
+      ok = false;
+    } else {
+      p->ctl = reinterpret_cast<Control*>(c);
+      p->counters = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(c) + sizeof(Control));
+      ok = cudaMemset(c, 0, sizeof(Control) + words * sizeof(unsigned int)) == cudaSuccess;
+    }
+  }
+  if (!ok) {
+    cudaGetLastError();
+    free_plan(p);
+    return GBFFT_ERR_ALLOC;
+  }
+  *out = p;
+  return GBFFT_OK;
+}
+
+void gbfft_plan_destroy(gbfft_plan plan) { free_plan(plan); }
+
+static int check_ptrs(const void* in, const void* out) {
+  if (!in || !out) return GBFFT_ERR_INVALID_ARG;
+  if (in == out) return GBFFT_ERR_INPLACE;
+  if (((uintptr_t)in) % 16 != 0 || ((uintptr_t)out) % 16 != 0) return GBFFT_ERR_ALIGNMENT;
+  return GBFFT_OK;
+}
+
+static Buf ws_buf(gbfft_plan_s* p, int i) {
+  if (!p->ws || i >= p->n_ws) return Buf{nullptr, 0};
+  return Buf{reinterpret_cast<char*>(p->ws) + (size_t)i * spectrum_bytes(p),
+             (long long)(spectrum_bytes(p) / sizeof(float2))};
+}
+
+static size_t op_in_bytes(const gbfft_plan_s* p, int op);
+static size_t op_out_bytes(const gbfft_plan_s* p, int op);
+
+int gbfft_exec(gbfft_plan plan, int op, const void* in, void* out, void* stream) {
+  if (!plan) return GBFFT_ERR_INVALID_ARG;
+  if (op < GBFFT_OP_FORWARD || op > GBFFT_OP_INVERSE_ADJOINT) return GBFFT_ERR_INVALID_ARG;
+  int rc = check_ptrs(in, out);
+  if (rc) return rc;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  rc = ensure_workspace(plan);
+  if (rc) return rc;
+  const int pipe = pipe_of(op);
+  Buf bin{const_cast<void*>(in), (long long)(op_in_bytes(plan, op) / sizeof(float2))};
+  Buf bout{out, (long long)(op_out_bytes(plan, op) / sizeof(float2))};
+  Pipeline P = build_pipeline(plan, pipe, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
+  return run_pipeline(plan, P, pipe, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gbfft_exec_forward(gbfft_plan plan, const void* in, void* out, void* stream) {
+  return gbfft_exec(plan, GBFFT_OP_FORWARD, in, out, stream);
+}
+int gbfft_exec_inverse(gbfft_plan plan, const void* in, void* out, void* stream) {
+  return gbfft_exec(plan, GBFFT_OP_INVERSE, in, out, stream);
+}
+int gbfft_exec_adjoint(gbfft_plan plan, const void* in, void* out, void* stream) {
+  return gbfft_exec(plan, GBFFT_OP_ADJOINT, in, out, stream);
+}
+int gbfft_exec_inverse_adjoint(gbfft_plan plan, const void* in, void* out, void* stream) {
+  return gbfft_exec(plan, GBFFT_OP_INVERSE_ADJOINT, in, out, stream);
+}
+
+int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream) {
+  if (!plan) return GBFFT_ERR_INVALID_ARG;
+  if (plan->kind != GBFFT_R2C || plan->batch < 1) return GBFFT_ERR_INVALID_ARG;
+  if (!find_stage(plan->nz, -1, kPoissonZ)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  int rc = check_ptrs(in, out);
+  if (rc) return rc;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  rc = ensure_workspace(plan);
+  if (rc) return rc;
+  Buf bin{const_cast<void*>(in), (long long)(op_in_bytes(plan, 4) / sizeof(float2))};
+  Buf bout{out, (long long)(op_out_bytes(plan, 4) / sizeof(float2))};
+  Pipeline P = build_pipeline(plan, kPipePoisson, 4, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
+  return run_pipeline(plan, P, kPipePoisson, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static size_t op_in_bytes(const gbfft_plan_s* p, int op) {
+  const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);  // rowA complex per row
+  const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
+  if (p->kind == GBFFT_C2C) return spec_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4) return real_b;
+  return spec_b;
+}
+
+static size_t op_out_bytes(const gbfft_plan_s* p, int op) {
+  const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);
+  const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
+  if (p->kind == GBFFT_C2C) return spec_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT) return spec_b;
+  return real_b;
+}
+
+int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out) {
+  if (!plan || !host_in || !host_out) return GBFFT_ERR_INVALID_ARG;
+  if (op < 0 || op > 4) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  const size_t ib = op_in_bytes(plan, op), ob = op_out_bytes(plan, op);
+  if (!plan->h_stream && cudaStreamCreateWithFlags(&plan->h_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return GBFFT_ERR_CUDA;
+  const size_t big = std::max(op_in_bytes(plan, 0), op_out_bytes(plan, 0));
+  if (!plan->h_in_dev) {
+    if (cudaMalloc(&plan->h_in_dev, big) != cudaSuccess || cudaMalloc(&plan->h_out_dev, big) != cudaSuccess) {
+      cudaGetLastError();
+      return GBFFT_ERR_ALLOC;
+    }
+    plan->h_in_bytes = plan->h_out_bytes = big;
+  }
+  cudaStream_t s = plan->h_stream;
+  if (cudaMemcpyAsync(plan->h_in_dev, host_in, ib, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return GBFFT_ERR_CUDA;
+  int rc = op == 4 ? gbfft_exec_poisson(plan, plan->h_in_dev, plan->h_out_dev, s)
+                   : gbfft_exec(plan, op, plan->h_in_dev, plan->h_out_dev, s);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(host_out, plan->h_out_dev, ob, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return GBFFT_ERR_CUDA;
+  return cuda_err(cudaStreamSynchronize(s));
+}
+
+int gbfft_get_device_error(gbfft_plan plan, int* code) {
+  if (!plan || !code) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GBFFT_ERR_CUDA;
+  Control c;
+  if (cudaMemcpy(&c, plan->ctl, sizeof(Control), cudaMemcpyDeviceToHost) != cudaSuccess) return GBFFT_ERR_CUDA;
+  *code = c.error == kDevErrTimeout ? GBFFT_ERR_TIMEOUT : (c.error ? GBFFT_ERR_CUDA : GBFFT_OK);
+  if (cudaMemset(plan->ctl, 0, sizeof(Control)) != cudaSuccess) return GBFFT_ERR_CUDA;
+  return GBFFT_OK;
+}
+
+int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* stream) {
+  if (!plan) return GBFFT_ERR_INVALID_ARG;
+  int rc = check_ptrs(in, out);
+  if (rc) return rc;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  const bool fwd = step >= 1 && step <= 6;
+  const bool inv = step >= 11 && step <= 16;
+  if (!fwd && !inv) return GBFFT_ERR_INVALID_ARG;
+  const int local = fwd ? step : step - 10;
+  const bool identity = (local % 2) == 0;
+  const int which = (local - 1) / 2;  // forward: 0 x, 1 y, 2 z; inverse: 0 z, 1 y, 2 x
+  if (identity && plan->kind == GBFFT_R2C && ((fwd && which == 0) || (inv && which == 2)))
+    return GBFFT_ERR_INVALID_ARG;
+  if (is_slab(plan)) return GBFFT_ERR_INVALID_ARG;
+  // pencil stage descriptors; only the selected stage's buffers matter
+  gbfft_plan_s tmp = *plan;
+  tmp.flags &= ~GBFFT_TRANSPOSED_OUT;
+  const Buf none{nullptr, -1};
+  Pipeline P = build_pipeline(&tmp, fwd ? kPipeFwd : kPipeInv, fwd ? GBFFT_OP_FORWARD : GBFFT_OP_ADJOINT, none,
+                              none, none, none);
+  StageDesc d = P.st[which];
+  d.in = reinterpret_cast<const float2*>(in);
+  d.out = reinterpret_cast<float2*>(out);
+  d.scale = 1.f;
+  d.interior = 1.f;
+  d.dep_rule = kDepNone;
+  if (identity) d.kind = kIdentity, d.dir = -1, d.n_in = d.n_out = d.L;
+  return launch_stage(d, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------- plan cache
+
+static std::mutex g_cache_mu;
+static std::map<std::tuple<int, int, int, int, int, int, int, unsigned>, gbfft_plan> g_cache;
+
+int gbfft_plan_get_cached(gbfft_plan* out, int nx, int ny, int nz, int kind, int dtype, int batch,
+                          unsigned flags) {
+  if (!out) return GBFFT_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GBFFT_ERR_NO_DEVICE;
+  }
+  auto key = std::make_tuple(dev, nx, ny, nz, kind, dtype, batch, flags);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_cache.find(key);
+  if (it != g_cache.end()) {
+    *out = it->second;
+    return GBFFT_OK;
+  }
+  gbfft_plan p = nullptr;
+  int rc = gbfft_plan_create(&p, nx, ny, nz, kind, dtype, batch, flags);
+  if (rc) {
+    *out = nullptr;
+    return rc;
+  }
+  g_cache[key] = p;
+  *out = p;
+  return GBFFT_OK;
+}
+
+void gbfft_plan_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto& kv : g_cache) free_plan(kv.second);
+  g_cache.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,595 @@
+// Device code of the staged 3D FFT: radix plans, butterflies, and the tile
+// processor that one stage of the paper's pencil sequence runs per pencil tile.
+//
+// Paper mapping (arxiv 2601.12209):
+//  * Section III-A: the 3D FFT is N_y N_z length-N_x transforms, a
+//    redistribution, N_x N_z length-N_y transforms, a redistribution, and
+//    N_x N_y length-N_z transforms. One tile = 16 pencils of one stage.
+//  * Algorithm 2 (pack -> exchange -> unpack): on one GPU the exchange is HBM
+//    itself; the pack is the tile's transposed store and the unpack the next
+//    stage's tile load. Both move 16 consecutive complex values (128 bytes)
+//    per transform index on the strided side, so every HBM access is a full
+//    128-byte line.
+//  * The 1D transforms are Stockham auto-sort passes of radix 2/3/4/5/8/16
+//    held in registers, with one shared-memory exchange between passes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbfft_internal.h"
+
+namespace gbfft {
+
+// ------------------------------------------------------------ radix plans
+
+struct Radices {
+  int n;
+  int r[12];
+};
+
+// Factor L into Stockham passes: powers of two split into as few, as even
+// passes as possible from {2,4,8,16}; then one pass per factor 3 and 5.
+__host__ __device__ constexpr Radices make_radices(int L) {
+  Radices R{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}};
+  int m = L;
+  int a = 0;
+  while (m % 2 == 0) {
+    ++a;
+    m /= 2;
+  }
+  if (a > 0) {
+    int passes = (a + 3) / 4;
+    int base = a / passes, extra = a % passes;
+    for (int i = 0; i < passes; ++i) R.r[R.n++] = 1 << (base + (i < extra ? 1 : 0));
+  }
+  while (m % 3 == 0) {
+    R.r[R.n++] = 3;
+    m /= 3;
+  }
+  while (m % 5 == 0) {
+    R.r[R.n++] = 5;
+    m /= 5;
+  }
+  if (m != 1) R.n = -1;  // unsupported prime factor
+  return R;
+}
+
+__host__ __device__ constexpr int radix_prefix(int L, int pass) {
+  int ns = 1;
+  for (int i = 0; i < pass; ++i) ns *= make_radices(L).r[i];
+  return ns;
+}
+
+// Groups of 16 threads that share the butterflies of a pass: the largest
+// power of two not above the smallest butterfly count of any pass, capped at
+// 32 (512 threads).
+__host__ __device__ constexpr int groups_for(int L) {
+  Radices R = make_radices(L);
+  int mn = L;
+  for (int i = 0; i < R.n; ++i) mn = (L / R.r[i]) < mn ? (L / R.r[i]) : mn;
+  int g = 1;
+  while (g * 2 <= mn && g * 2 <= 32) g *= 2;
+  return g;
+}
+
+__host__ __device__ constexpr int threads_for(int L) { return 16 * groups_for(L); }
+
+// Blocks per SM the register allocation must allow: two 512-thread blocks
+// (64 registers) so one block's HBM phase overlaps the other's arithmetic;
+// length 1024 keeps one block (32 complex values per thread).
+__host__ __device__ constexpr int min_blocks_for(int L) {
+  return L >= 1024 ? 1 : (threads_for(L) >= 512 ? 2 : (threads_for(L) >= 256 ? 3 : 4));
+}
+
+// ---------------------------------------------------------- complex helpers
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by s*i, s = +1 or -1
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// twiddle from the forward-sign table, conjugated for the inverse direction
+template <int DIR>
+__device__ __forceinline__ float2 tw_dir(float2 w) {
+  return DIR < 0 ? w : make_float2(w.x, -w.y);
+}
+
+// --------------------------------------------------------------- butterflies
+// In-register DFT of length R with sign DIR: y[q] = sum_r x[r] exp(DIR 2 pi i rq/R).
+// Constants are cos/sin of multiples of 2 pi/R written to 20 digits.
+
+template <int DIR>
+__device__ __forceinline__ void dft2(float2* a) {
+  float2 t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2* a) {
+  float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+  float2 t2 = cadd(a[1], a[3]), t3 = mul_si<DIR>(csub(a[1], a[3]));
+  a[0] = cadd(t0, t2);
+  a[2] = csub(t0, t2);
+  a[1] = cadd(t1, t3);
+  a[3] = csub(t1, t3);
+}
+
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+
+// multiply by exp(DIR 2 pi i m/8) for m = 1, 2, 3
+template <int DIR, int M>
+__device__ __forceinline__ float2 w8(float2 a) {
+  if constexpr (M == 0) {
+    return a;
+  } else if constexpr (M == 2) {
+    return mul_si<DIR>(a);
+  } else if constexpr (M == 1) {  // (1 + DIR i)/sqrt2
+    float2 t = mul_si<DIR>(a);
+    return make_float2((a.x + t.x) * kSqrtHalf, (a.y + t.y) * kSqrtHalf);
+  } else {  // M == 3: (-1 + DIR i)/sqrt2
+    float2 t = mul_si<DIR>(a);
+    return make_float2((t.x - a.x) * kSqrtHalf, (t.y - a.y) * kSqrtHalf);
+  }
+}
+
+// radix-8 as radix-2 then two radix-4: X[2q] = DFT4(a_r + a_{r+4}),
+// X[2q+1] = DFT4((a_r - a_{r+4}) w8^r).
+template <int DIR>
+__device__ __forceinline__ void dft8(float2* a) {
+  float2 e[4], o[4];
+  e[0] = cadd(a[0], a[4]);
+  o[0] = csub(a[0], a[4]);
+  e[1] = cadd(a[1], a[5]);
+  o[1] = w8<DIR, 1>(csub(a[1], a[5]));
+  e[2] = cadd(a[2], a[6]);
+  o[2] = w8<DIR, 2>(csub(a[2], a[6]));
+  e[3] = cadd(a[3], a[7]);
+  o[3] = w8<DIR, 3>(csub(a[3], a[7]));
+  dft4<DIR>(e);
+  dft4<DIR>(o);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a[2 * q] = e[q];
+    a[2 * q + 1] = o[q];
+  }
+}
+
+// cos and sin of 2 pi m / 16, m = 1..3
+constexpr float kC16_1 = 0.92387953251128675613f;
+constexpr float kS16_1 = 0.38268343236508977173f;
+
+// multiply by exp(DIR 2 pi i m/16), m in [0, 8)
+template <int DIR, int M>
+__device__ __forceinline__ float2 w16(float2 a) {
+  if constexpr (M % 2 == 0) {
+    return w8<DIR, M / 2>(a);
+  } else {
+    // exp(DIR i theta) with theta = 2 pi M / 16
+    constexpr float c = (M == 1) ? kC16_1 : (M == 3) ? kS16_1 : (M == 5) ? -kS16_1 : -kC16_1;
+    constexpr float s = (M == 1) ? kS16_1 : (M == 3) ? kC16_1 : (M == 5) ? kC16_1 : kS16_1;
+    constexpr float sd = DIR < 0 ? -s : s;
+    return make_float2(fmaf(a.x, c, -a.y * sd), fmaf(a.x, sd, a.y * c));
+  }
+}
+
+// radix-16 as radix-2 then two radix-8.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* a) {
+  float2 e[8], o[8];
+  e[0] = cadd(a[0], a[8]);
+  o[0] = csub(a[0], a[8]);
+  e[1] = cadd(a[1], a[9]);
+  o[1] = w16<DIR, 1>(csub(a[1], a[9]));
+  e[2] = cadd(a[2], a[10]);
+  o[2] = w16<DIR, 2>(csub(a[2], a[10]));
+  e[3] = cadd(a[3], a[11]);
+  o[3] = w16<DIR, 3>(csub(a[3], a[11]));
+  e[4] = cadd(a[4], a[12]);
+  o[4] = w16<DIR, 4>(csub(a[4], a[12]));
+  e[5] = cadd(a[5], a[13]);
+  o[5] = w16<DIR, 5>(csub(a[5], a[13]));
+  e[6] = cadd(a[6], a[14]);
+  o[6] = w16<DIR, 6>(csub(a[6], a[14]));
+  e[7] = cadd(a[7], a[15]);
+  o[7] = w16<DIR, 7>(csub(a[7], a[15]));
+  dft8<DIR>(e);
+  dft8<DIR>(o);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    a[2 * q] = e[q];
+    a[2 * q + 1] = o[q];
+  }
+}
+
+// radix-3: X0 = a0 + t, X1,2 = a0 - t/2 +- DIR i (sqrt3/2)(a1 - a2), t = a1 + a2
+template <int DIR>
+__device__ __forceinline__ void dft3(float2* a) {
+  constexpr float h = 0.86602540378443864676f;  // sqrt(3)/2
+  float2 t = cadd(a[1], a[2]);
+  float2 u = mul_si<DIR>(cscale(csub(a[1], a[2]), h));
+  float2 m = make_float2(fmaf(-0.5f, t.x, a[0].x), fmaf(-0.5f, t.y, a[0].y));
+  a[0] = cadd(a[0], t);
+  a[1] = cadd(m, u);
+  a[2] = csub(m, u);
+}
+
+// radix-5 with t1 = a1+a4, t2 = a2+a3, d1 = a1-a4, d2 = a2-a3.
+template <int DIR>
+__device__ __forceinline__ void dft5(float2* a) {
+  constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi/5)
+  constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi/5)
+  constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi/5)
+  constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi/5)
+  float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+  float2 d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+  float2 a0 = a[0];
+  float2 r1 = make_float2(a0.x + c1 * t1.x + c2 * t2.x, a0.y + c1 * t1.y + c2 * t2.y);
+  float2 r2 = make_float2(a0.x + c2 * t1.x + c1 * t2.x, a0.y + c2 * t1.y + c1 * t2.y);
+  float2 i1 = mul_si<DIR>(make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
+  float2 i2 = mul_si<DIR>(make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+  a[0] = make_float2(a0.x + t1.x + t2.x, a0.y + t1.y + t2.y);
+  a[1] = cadd(r1, i1);
+  a[4] = csub(r1, i1);
+  a[2] = cadd(r2, i2);
+  a[3] = csub(r2, i2);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2* a) {
+  if constexpr (R == 2) dft2<DIR>(a);
+  else if constexpr (R == 3) dft3<DIR>(a);
+  else if constexpr (R == 4) dft4<DIR>(a);
+  else if constexpr (R == 5) dft5<DIR>(a);
+  else if constexpr (R == 8) dft8<DIR>(a);
+  else if constexpr (R == 16) dft16<DIR>(a);
+}
+
+// ------------------------------------------------------------ memory helpers
+
+// Tile layout in shared memory: element n of pencil p at n*16 + swizzled p.
+// The 16 pencils of one index n form one 128-byte row; the 16-byte chunk
+// (pencil pair) index is XOR-ed with n mod 8, so both "16 pencils at one n"
+// and "one pencil pair over 8 consecutive n" touch every bank once.
+__device__ __forceinline__ int swz(int n, int p) { return (n << 4) | ((((p >> 1) ^ (n & 7)) << 1) | (p & 1)); }
+
+__device__ __forceinline__ float2 ld_data(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ void st_data(float2* p, float2 v) { __stcg(p, v); }
+
+struct TileIO {
+  const float2* gin;
+  float2* gout;
+  long long in_g, in_n, out_g, out_n;
+  int valid;
+  float scale;
+};
+
+// Row-side load: the transform axis is contiguous in global memory. Lanes run
+// along n (coalesced), each lane moves one pencil pair as a 16-byte smem chunk.
+template <int THREADS, int NROWS>
+__device__ __forceinline__ void row_load(float2* sm, const TileIO& io) {
+  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
+    int n = it % NROWS, pair = it / NROWS;
+    int p0 = 2 * pair;
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    if (p0 < io.valid) a = ld_data(io.gin + p0 * io.in_g + n);
+    if (p0 + 1 < io.valid) b = ld_data(io.gin + (p0 + 1) * io.in_g + n);
+    *reinterpret_cast<float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1))) = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+template <int THREADS, int NROWS>
+__device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
+  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
+    int n = it % NROWS, pair = it / NROWS;
+    int p0 = 2 * pair;
+    float4 v = *reinterpret_cast<const float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1)));
+    if (p0 < io.valid) st_data(io.gout + p0 * io.out_g + n, make_float2(v.x * io.scale, v.y * io.scale));
+    if (p0 + 1 < io.valid) st_data(io.gout + (p0 + 1) * io.out_g + n, make_float2(v.z * io.scale, v.w * io.scale));
+  }
+}
+
+// Column-side load/store: 16 consecutive pencils are contiguous; lanes run
+// along p, so 16 lanes move one 128-byte line.
+template <int THREADS, int NROWS>
+__device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
+  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
+    int p = it & 15, n = it >> 4;
+    float2 a = make_float2(0.f, 0.f);
+    if (p < io.valid) a = ld_data(io.gin + p + n * io.in_n);
+    sm[swz(n, p)] = a;
+  }
+}
+
+template <int THREADS, int NROWS>
+__device__ __forceinline__ void col_store(const float2* sm, const TileIO& io) {
+  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
+    int p = it & 15, n = it >> 4;
+    if (p < io.valid) {
+      float2 v = sm[swz(n, p)];
+      st_data(io.gout + p + n * io.out_n, make_float2(v.x * io.scale, v.y * io.scale));
+    }
+  }
+}
+
+// ---------------------------------------------------------- Stockham passes
+
+// One Stockham pass of radix R over the 16 pencils of the tile.
+// Butterfly j (0 <= j < L/R) of pencil p reads x[j + r L/R], applies the
+// twiddles W_{Ns R}^{r k} (k = j mod Ns), a radix-R DFT, and writes
+// y[(j - k) R + k + q Ns]. Thread (p, g) owns butterflies j = g + t*G.
+//   SRC_GLOBAL: pass 0 reads the column-side input straight from HBM.
+//   DST_GLOBAL: the last pass writes the column-side output straight to HBM.
+template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, bool SYNC_BEFORE_WRITE>
+__device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, const TileIO& io) {
+  constexpr Radices RP = make_radices(L);
+  constexpr int R = RP.r[PASS];
+  constexpr int Ns = radix_prefix(L, PASS);
+  constexpr int NB = L / R;
+  constexpr int S = L / (Ns * R);
+  constexpr int G = THREADS / 16;
+  constexpr int NBT = (NB + G - 1) / G;
+  const int p = threadIdx.x & 15, g = threadIdx.x >> 4;
+  float2 v[NBT][R];
+#pragma unroll
+  for (int t = 0; t < NBT; ++t) {
+    const int j = g + t * G;
+    if (NB % G == 0 || j < NB) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = j + r * NB;
+        if constexpr (SRC_GLOBAL) {
+          v[t][r] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
+        } else {
+          v[t][r] = sm[swz(n, p)];
+        }
+      }
+      if constexpr (Ns > 1) {
+        const int k = j % Ns;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[t][r] = cmul(v[t][r], tw_dir<DIR>(tw[r * k * S]));
+      }
+      dft<R, DIR>(v[t]);
+    }
+  }
+  if constexpr (DST_GLOBAL) {
+    if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NBT; ++t) {
+      const int j = g + t * G;
+      if ((NB % G == 0 || j < NB) && p < io.valid) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int n = j + q * NB;  // last pass: Ns R = L
+          st_data(io.gout + p + n * io.out_n, make_float2(v[t][q].x * io.scale, v[t][q].y * io.scale));
+        }
+      }
+    }
+  } else {
+    if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NBT; ++t) {
+      const int j = g + t * G;
+      if (NB % G == 0 || j < NB) {
+        const int k = j % Ns;
+#pragma unroll
+        for (int q = 0; q < R; ++q) sm[swz((j - k) * R + k + q * Ns, p)] = v[t][q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// All passes of a length-L transform. The data starts in shared memory unless
+// SRC_GLOBAL, and ends in shared memory unless DST_GLOBAL.
+template <int L, int DIR, int THREADS, bool SRC_GLOBAL, bool DST_GLOBAL, bool INPLACE_GLOBAL, int PASS = 0>
+__device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const TileIO& io) {
+  constexpr int NP = make_radices(L).n;
+  if constexpr (PASS < NP) {
+    constexpr bool src_g = SRC_GLOBAL && PASS == 0;
+    constexpr bool dst_g = DST_GLOBAL && PASS == NP - 1;
+    // before overwriting shared memory, everyone must have read it; a direct
+    // global->global single pass in place also needs the barrier
+    constexpr bool sync_w = (!src_g && !dst_g) || (src_g && dst_g && INPLACE_GLOBAL);
+    stockham_pass<L, DIR, THREADS, PASS, src_g, dst_g, sync_w>(sm, tw, io);
+    fft_passes<L, DIR, THREADS, SRC_GLOBAL, DST_GLOBAL, INPLACE_GLOBAL, PASS + 1>(sm, tw, io);
+  }
+}
+
+// ---------------------------------------------------- real-transform phases
+
+// R2C split (in place in shared memory, rows 0..M): the length-M FFT Z of
+// z[m] = x[2m] + i x[2m+1] becomes X[k] = Ze[k] + W_2M^k Zo[k], k = 0..M, with
+// Ze = (Z[k] + conj Z[M-k])/2, Zo = (Z[k] - conj Z[M-k])/(2i). Pairs (k, M-k)
+// are handled by one thread. Bins 1..M-1 are scaled by `interior`.
+template <int M, int THREADS>
+__device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float interior) {
+  constexpr int NPAIR = M / 2 + 1;
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    if (k == 0) {
+      float2 z0 = sm[swz(0, p)];
+      sm[swz(0, p)] = make_float2(z0.x + z0.y, 0.f);
+      sm[swz(M, p)] = make_float2(z0.x - z0.y, 0.f);
+    } else if (2 * k < M) {
+      float2 A = sm[swz(k, p)], B = sm[swz(M - k, p)];
+      float2 ze = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+      float2 zo = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+      float2 t = cmul(tw2[k], zo);
+      float2 xk = cadd(ze, t);
+      float2 xm = cconj(csub(ze, t));
+      sm[swz(k, p)] = cscale(xk, interior);
+      sm[swz(M - k, p)] = cscale(xm, interior);
+    } else if (2 * k == M) {
+      float2 A = sm[swz(k, p)];
+      sm[swz(k, p)] = cscale(cconj(A), interior);
+    }
+  }
+  __syncthreads();
+}
+
+// C2R merge (in place, reads rows 0..M, writes rows 0..M-1): with
+// E = X[k] + conj X[M-k] and O = (X[k] - conj X[M-k]) exp(+i pi k/M),
+// Z[k] = E + i O; the inverse length-M FFT of Z gives x[2m] + i x[2m+1].
+// Only the real parts of X[0] and X[M] enter (the Hermitian projection).
+template <int M, int THREADS>
+__device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float interior) {
+  constexpr int NPAIR = M / 2 + 1;
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    if (k == 0) {
+      float a = sm[swz(0, p)].x, c = sm[swz(M, p)].x;
+      sm[swz(0, p)] = make_float2(a + c, a - c);
+    } else if (2 * k < M) {
+      float2 xk = cscale(sm[swz(k, p)], interior), xm = cscale(sm[swz(M - k, p)], interior);
+      float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+      float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+      float2 o = cmul(d, cconj(tw2[k]));
+      sm[swz(k, p)] = make_float2(e.x - o.y, e.y + o.x);
+      sm[swz(M - k, p)] = make_float2(e.x + o.y, -e.y + o.x);
+    } else if (2 * k == M) {
+      float2 xk = cscale(sm[swz(k, p)], interior);
+      sm[swz(k, p)] = make_float2(2.f * xk.x, -2.f * xk.y);
+    }
+  }
+  __syncthreads();
+}
+
+// Poisson multiplier -1/|k|^2 (k = 0 -> 0) on the z pencils of the R2C half
+// spectrum, folded with the 1/N of the inverse. Pencil p has kx = gfirst + p,
+// the tile's outer index is ky, row n is kz.
+template <int L, int THREADS>
+__device__ __forceinline__ void poisson_multiply(float2* sm, int gfirst, int ky_idx, int ny, float inv_n) {
+  const float ky = (float)(ky_idx <= ny / 2 ? ky_idx : ky_idx - ny);
+  for (int it = threadIdx.x; it < L * 16; it += THREADS) {
+    const int p = it & 15, n = it >> 4;
+    const float kx = (float)(gfirst + p);
+    const float kz = (float)(n <= L / 2 ? n : n - L);
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    const float m = k2 > 0.f ? -inv_n / k2 : 0.f;
+    float2 v = sm[swz(n, p)];
+    sm[swz(n, p)] = make_float2(v.x * m, v.y * m);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- tile driver
+
+template <int L, int DIR, int KIND>
+struct TileShape {
+  static constexpr int kThreads = threads_for(L);
+  static constexpr int kRows = L + 1;  // one spare row for the Nyquist bin of R2C/C2R
+  static constexpr int kSmemTile = kRows * kTileP;  // float2 elements
+};
+
+__device__ __forceinline__ TileIO make_io(const StageDesc& d, long long tile, int& o_out, int& g0_out) {
+  TileIO io;
+  const long long gc = tile % d.n_gchunks;
+  const long long rest = tile / d.n_gchunks;
+  const int o = (int)(rest % d.n_outer);
+  const int b = (int)(rest / d.n_outer);
+  const int g0 = (int)gc * kTileP;
+  io.valid = min(kTileP, d.n_group - g0);
+  io.gin = d.in + b * d.in_b + o * d.in_o + g0 * d.in_g;
+  io.gout = d.out + b * d.out_b + o * d.out_o + g0 * d.out_g;
+  io.in_g = d.in_g;
+  io.in_n = d.in_n;
+  io.out_g = d.out_g;
+  io.out_n = d.out_n;
+  io.scale = d.scale;
+  o_out = o;
+  g0_out = g0;
+  return io;
+}
+
+// Process one tile of one stage. THREADS may exceed threads_for(L) (the
+// persistent kernel runs several lengths with one block size); the extra
+// groups then share the butterflies.
+template <int L, int DIR, int KIND, int THREADS>
+__device__ __forceinline__ void process_tile(const StageDesc& d, long long tile, float2* sm, const float2* tw,
+                                             const float2* tw2) {
+  int o, g0;
+  TileIO io = make_io(d, tile, o, g0);
+  const bool row_in = d.in_mode == kRow, row_out = d.out_mode == kRow;
+  const bool inplace = d.in == d.out;
+
+  if constexpr (KIND == kIdentity) {
+    // pure redistribution: unpack into the tile, pack out of it
+    if (row_in) row_load<THREADS, L>(sm, io);
+    else col_load<THREADS, L>(sm, io);
+    __syncthreads();
+    if (row_out) row_store<THREADS, L>(sm, io);
+    else col_store<THREADS, L>(sm, io);
+  } else if constexpr (KIND == kPlain) {
+    if (row_in) {
+      row_load<THREADS, L>(sm, io);
+      __syncthreads();
+      if (row_out) {
+        fft_passes<L, DIR, THREADS, false, false, false>(sm, tw, io);
+        row_store<THREADS, L>(sm, io);
+      } else {
+        fft_passes<L, DIR, THREADS, false, true, false>(sm, tw, io);
+      }
+    } else {
+      if (row_out) {
+        fft_passes<L, DIR, THREADS, true, false, false>(sm, tw, io);
+        row_store<THREADS, L>(sm, io);
+      } else if (inplace) {
+        fft_passes<L, DIR, THREADS, true, true, true>(sm, tw, io);
+      } else {
+        fft_passes<L, DIR, THREADS, true, true, false>(sm, tw, io);
+      }
+    }
+  } else if constexpr (KIND == kR2CPost) {
+    // real rows viewed as L complex pairs -> L+1 half-spectrum bins
+    row_load<THREADS, L>(sm, io);
+    __syncthreads();
+    fft_passes<L, -1, THREADS, false, false, false>(sm, tw, io);
+    r2c_post<L, THREADS>(sm, tw2, d.interior);
+    if (row_out) row_store<THREADS, L + 1>(sm, io);
+    else col_store<THREADS, L + 1>(sm, io);
+  } else if constexpr (KIND == kC2RPre) {
+    // L+1 half-spectrum bins -> L complex pairs of real output
+    if (row_in) row_load<THREADS, L + 1>(sm, io);
+    else col_load<THREADS, L + 1>(sm, io);
+    __syncthreads();
+    c2r_pre<L, THREADS>(sm, tw2, d.interior);
+    fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io);
+    row_store<THREADS, L>(sm, io);
+  } else if constexpr (KIND == kPoissonZ) {
+    // z pencils of the half spectrum: forward, multiply, inverse, in one tile
+    TileIO io_nos = io;
+    io_nos.scale = 1.f;
+    if (row_in) {
+      row_load<THREADS, L>(sm, io);
+      __syncthreads();
+      fft_passes<L, -1, THREADS, false, false, false>(sm, tw, io_nos);
+    } else {
+      fft_passes<L, -1, THREADS, true, false, false>(sm, tw, io_nos);
+    }
+    poisson_multiply<L, THREADS>(sm, g0, o, d.pz_ny, d.scale);
+    if (row_out) {
+      fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io_nos);
+      row_store<THREADS, L>(sm, io_nos);
+    } else {
+      fft_passes<L, +1, THREADS, false, true, false>(sm, tw, io_nos);
+    }
+  }
+}
+
+// Copy a stage's twiddle tables into shared memory.
+template <int L, int THREADS>
+__device__ __forceinline__ void load_twiddles(float2* tw_s, float2* tw2_s, const StageDesc& d, bool need_tw2) {
+  for (int i = threadIdx.x; i < L; i += THREADS) tw_s[i] = d.tw[i];
+  if (need_tw2)
+    for (int i = threadIdx.x; i <= L; i += THREADS) tw2_s[i] = d.tw2[i];
+}
+
+}  // namespace gbfft

@@ -1,0 +1,83 @@
+// Internal types shared by the host plan code and the kernel translation units.
+// Not part of the public C ABI (include/gbfft.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbfft {
+
+// Pencils per tile. A tile is 16 pencils x the transform length; on the
+// strided ("column") side of a stage the 16 pencils are 16 consecutive complex
+// values = one 128-byte line per transform index.
+constexpr int kTileP = 16;
+
+enum AccessMode : int {
+  kRow = 0,  // the transform axis is contiguous (element stride 1)
+  kCol = 1,  // the 16 pencils of a tile are contiguous (pencil stride 1)
+};
+
+enum TileKind : int {
+  kPlain = 0,     // complex transform of length L
+  kR2CPost = 1,   // length-L complex FFT of real pairs, then split into L+1 bins
+  kC2RPre = 2,    // merge L+1 half-spectrum bins into L complex, then FFT
+  kIdentity = 3,  // no arithmetic: pure pack/transpose/unpack (debug, bit-exact tests)
+  kPoissonZ = 4,  // forward FFT, multiply by -1/|k|^2, inverse FFT (fused Poisson z stage)
+};
+
+// Dependency rule of a tile on the previous stage of the same launch
+// (persistent kernel only). See DepRule handling in the persistent kernel.
+enum DepRule : int {
+  kDepNone = 0,
+  kDepGroup = 1,       // group range [g0, g0+valid) <-> producer outer ids
+  kDepOuter = 2,       // outer id o <-> producer outer id o
+  kDepGchunkOfOuter = 3,  // outer id o <-> producer group chunk o/16
+  kDepSameGchunk = 4,  // own group chunk <-> producer group chunk
+  kDepAll = 5,         // every producer tile of the same batch entry
+};
+
+// One stage of the staged 3D FFT: a batched 1D transform over pencils,
+// reading one layout and writing another (the pack/transpose/unpack of the
+// redistribution is the load and store of the tile).
+//
+// Tile t decodes as t = (b * n_outer + o) * n_gchunks + gc. Element n of
+// pencil p of the tile is read at
+//   in  + b*in_b  + o*in_o  + (16*gc + p)*in_g  + n*in_n
+// and output element k written at
+//   out + b*out_b + o*out_o + (16*gc + p)*out_g + k*out_n      (float2 units).
+struct StageDesc {
+  const float2* in;
+  float2* out;
+  long long in_b, in_o, in_g, in_n;
+  long long out_b, out_o, out_g, out_n;
+  long long n_tiles;
+  int batch, n_outer, n_group, n_gchunks;
+  int L;         // complex transform length of the pencil
+  int n_in;      // elements read per pencil (L, or L+1 for kC2RPre)
+  int n_out;     // elements written per pencil (L, or L+1 for kR2CPost)
+  int in_mode, out_mode, kind;
+  int dir;       // -1 forward sign, +1 inverse sign
+  float scale;     // multiplies every output value
+  float interior;  // R2C/C2R: multiplies bins 1..L-1 of the half spectrum
+  const float2* tw;    // W_L^t = exp(-2 pi i t / L), t in [0, L)   (device)
+  const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R only)
+  // Poisson z stage: wavenumber bookkeeping of the tile's pencils
+  int pz_nx, pz_ny;    // full grid nx, ny (kx of pencil = group index, ky = outer index)
+  // persistent-kernel dependency rule on the previous stage
+  int dep_rule;
+  int prev_n_outer, prev_n_gchunks;
+};
+
+// Control block of one persistent launch (device memory, zeroed before each launch).
+struct Control {
+  unsigned int ticket;
+  int error;         // first device-side error code (0 = none)
+  int abort;         // set with the error so other CTAs stop taking tickets
+  int pad;
+};
+
+constexpr int kMaxStages = 5;
+
+// Error codes written into Control::error by device code.
+constexpr int kDevErrTimeout = 1;
+
+}  // namespace gbfft

@@ -1,0 +1,261 @@
+// Kernel templates: one launch per stage (stage_kernel) and one persistent
+// launch for a whole transform (persistent_kernel), plus the registry entries
+// the host dispatches through.
+#pragma once
+#include <vector>
+
+#include "gbfft_device.cuh"
+
+namespace gbfft {
+
+// ------------------------------------------------------------- registry
+
+struct StageKernel {
+  int L, dir, kind;
+  const void* fn;
+  int threads;
+  size_t smem;
+};
+
+struct PersistentKernel {
+  int ncodes;
+  int codes[8];  // (L << 8) | (kind << 1) | (dir > 0)
+  const void* fn;
+  int threads;
+  size_t smem;               // tile bytes
+  size_t tw_smem_per_stage;  // twiddle bytes per stage (total = smem + nstages * this)
+};
+
+constexpr int kcode(int L, int kind, int dir) { return (L << 8) | (kind << 1) | (dir > 0 ? 1 : 0); }
+
+std::vector<StageKernel>& stage_registry();
+std::vector<PersistentKernel>& persistent_registry();
+
+// --------------------------------------------------------- stage kernel
+
+template <int L, int KIND>
+constexpr size_t stage_smem_bytes() {
+  return sizeof(float2) * ((size_t)(L + 1) * kTileP + L + (L + 1));
+}
+
+// One launch per stage. Each block loops over tiles with a grid stride, so
+// the twiddle tables are staged into shared memory once per block.
+template <int L, int DIR, int KIND>
+__global__ void __launch_bounds__(threads_for(L), min_blocks_for(L)) stage_kernel(StageDesc d) {
+  constexpr int THREADS = threads_for(L);
+  extern __shared__ float4 smem4[];
+  float2* sm = reinterpret_cast<float2*>(smem4);
+  float2* tw = sm + (L + 1) * kTileP;
+  float2* tw2 = tw + L;
+  load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre);
+  __syncthreads();
+  for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
+    process_tile<L, DIR, KIND, THREADS>(d, tile, sm, tw, tw2);
+    __syncthreads();
+  }
+}
+
+template <int L, int DIR, int KIND>
+StageKernel make_stage_entry() {
+  return StageKernel{L, DIR, KIND, reinterpret_cast<const void*>(&stage_kernel<L, DIR, KIND>), threads_for(L),
+                     stage_smem_bytes<L, KIND>()};
+}
+
+// ----------------------------------------------------- persistent kernel
+//
+// The paper's dynamic scheduler hands ready DTasks to idle workers
+// (Sections III-C, IV-C/D). Here every block is a worker: it takes the next
+// ticket from one atomic counter, looks the ticket up in a host-built
+// schedule (stage, tile) in an order where every dependency comes earlier,
+// waits (bounded) until the tiles it reads are complete, runs the tile, and
+// publishes its completion on per-outer, per-group-chunk and per-batch
+// counters -- the per-chunk dependency tracking of DataDepsTaskQueue
+// (Section IV-D) with counters instead of task graphs.
+
+struct PersistentArgs {
+  StageDesc st[kMaxStages];
+  int nstages;
+  const unsigned int* sched;   // ticket -> (stage << 28) | tile
+  unsigned int total;          // tickets
+  Control* ctl;
+  unsigned int* cnt_outer[kMaxStages];
+  unsigned int* cnt_gchunk[kMaxStages];
+  unsigned int* cnt_total[kMaxStages];
+  long long timeout_ns;        // bound on every dependency wait
+  int debug_never;             // wait for one more completion than exists (timeout test)
+};
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *p >= target. Returns false on timeout or abort.
+__device__ __forceinline__ bool wait_counter(const unsigned int* p, unsigned int target, const PersistentArgs& a,
+                                             unsigned long long t0) {
+  unsigned int spins = 0;
+  while (ld_acquire(p) < target) {
+    if ((++spins & 63) == 0) {
+      if (*reinterpret_cast<volatile int*>(&a.ctl->abort)) return false;
+      if ((long long)(global_ns() - t0) > a.timeout_ns) return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// Wait for the producer tiles (previous stage) that tile `tile` of stage s reads.
+__device__ __forceinline__ bool wait_deps(const PersistentArgs& a, int s, long long tile) {
+  if (s == 0) return true;
+  const StageDesc& d = a.st[s];
+  if (d.dep_rule == kDepNone) return true;
+  const long long gc = tile % d.n_gchunks;
+  const long long rest = tile / d.n_gchunks;
+  const int o = (int)(rest % d.n_outer);
+  const int b = (int)(rest / d.n_outer);
+  const unsigned int extra = a.debug_never ? 1u : 0u;
+  const unsigned long long t0 = global_ns();
+  switch (d.dep_rule) {
+    case kDepGroup: {
+      const int g0 = (int)gc * kTileP;
+      const int valid = min(kTileP, d.n_group - g0);
+      const unsigned int target = (unsigned int)d.prev_n_gchunks + extra;
+      for (int g = g0; g < g0 + valid; ++g)
+        if (!wait_counter(a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + g, target, a, t0)) return false;
+      return true;
+    }
+    case kDepOuter:
+      return wait_counter(a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + o,
+                          (unsigned int)d.prev_n_gchunks + extra, a, t0);
+    case kDepGchunkOfOuter:
+      return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + o / kTileP,
+                          (unsigned int)d.prev_n_outer + extra, a, t0);
+    case kDepSameGchunk:
+      return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + gc,
+                          (unsigned int)d.prev_n_outer + extra, a, t0);
+    case kDepAll:
+      return wait_counter(a.cnt_total[s - 1] + b,
+                          (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra, a, t0);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void signal_done(const PersistentArgs& a, int s, long long tile) {
+  const StageDesc& d = a.st[s];
+  const long long gc = tile % d.n_gchunks;
+  const long long rest = tile / d.n_gchunks;
+  const int o = (int)(rest % d.n_outer);
+  const int b = (int)(rest / d.n_outer);
+  __threadfence();
+  atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);
+  atomicAdd(a.cnt_gchunk[s] + (long long)b * d.n_gchunks + gc, 1u);
+  atomicAdd(a.cnt_total[s] + b, 1u);
+}
+
+// Runtime dispatch of one tile over the compile-time list of (L, kind, dir)
+// codes this kernel was built for.
+template <int THREADS, int CODE, int... REST>
+__device__ __forceinline__ void dispatch_tile(int code, const StageDesc& d, long long tile, float2* sm,
+                                              const float2* tw, const float2* tw2) {
+  if (code == CODE) {
+    constexpr int L = CODE >> 8, KIND = (CODE >> 1) & 127, DIR = (CODE & 1) ? 1 : -1;
+    process_tile<L, DIR, KIND, THREADS>(d, tile, sm, tw, tw2);
+  } else if constexpr (sizeof...(REST) > 0) {
+    dispatch_tile<THREADS, REST...>(code, d, tile, sm, tw, tw2);
+  }
+}
+
+template <int CODE, int... REST>
+__host__ __device__ constexpr int max_len() {
+  if constexpr (sizeof...(REST) == 0) return CODE >> 8;
+  else return (CODE >> 8) > max_len<REST...>() ? (CODE >> 8) : max_len<REST...>();
+}
+
+template <int CODE, int... REST>
+__host__ __device__ constexpr int max_threads() {
+  if constexpr (sizeof...(REST) == 0) return threads_for(CODE >> 8);
+  else return threads_for(CODE >> 8) > max_threads<REST...>() ? threads_for(CODE >> 8) : max_threads<REST...>();
+}
+
+// Shared memory of a persistent launch: the tile, then one twiddle block
+// (W_L, and W_2L for real transforms) per stage of the launch.
+template <int... CODES>
+constexpr size_t persistent_tile_bytes() {
+  return sizeof(float2) * (size_t)(max_len<CODES...>() + 1) * kTileP;
+}
+template <int... CODES>
+constexpr size_t persistent_tw_bytes_per_stage() {
+  return sizeof(float2) * (size_t)(2 * max_len<CODES...>() + 1);
+}
+
+__device__ __forceinline__ int stage_code(const StageDesc& d) {
+  return (d.L << 8) | (d.kind << 1) | (d.dir > 0 ? 1 : 0);
+}
+
+template <int... CODES>
+__global__ void __launch_bounds__(max_threads<CODES...>(), min_blocks_for(max_len<CODES...>()))
+persistent_kernel(PersistentArgs a) {
+  constexpr int THREADS = max_threads<CODES...>();
+  constexpr int LM = max_len<CODES...>();
+  extern __shared__ float4 smem4[];
+  float2* sm = reinterpret_cast<float2*>(smem4);
+  float2* tws = sm + (LM + 1) * kTileP;
+  __shared__ unsigned int s_ticket;
+  __shared__ int s_ok;
+  for (int s = 0; s < a.nstages; ++s) {
+    float2* tw = tws + s * (2 * LM + 1);
+    const StageDesc& d = a.st[s];
+    for (int i = threadIdx.x; i < d.L; i += THREADS) tw[i] = d.tw[i];
+    if (d.kind == kR2CPost || d.kind == kC2RPre)
+      for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[LM + i] = d.tw2[i];
+  }
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_ticket = atomicAdd(&a.ctl->ticket, 1u);
+      s_ok = *reinterpret_cast<volatile int*>(&a.ctl->abort) ? 0 : 1;
+      if (s_ok && s_ticket < a.total) {
+        const unsigned int e = a.sched[s_ticket];
+        if (!wait_deps(a, (int)(e >> 28), (long long)(e & 0x0FFFFFFFu))) {
+          atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
+          atomicExch(&a.ctl->abort, 1);
+          s_ok = 0;
+        }
+      }
+    }
+    __syncthreads();
+    const unsigned int t = s_ticket;
+    if (t >= a.total || !s_ok) break;
+    const unsigned int e = a.sched[t];
+    const int s = (int)(e >> 28);
+    const long long tile = (long long)(e & 0x0FFFFFFFu);
+    const StageDesc& d = a.st[s];
+    const float2* tw = tws + s * (2 * LM + 1);
+    dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile, sm, tw, tw + LM);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) signal_done(a, s, tile);
+  }
+}
+
+template <int... CODES>
+PersistentKernel make_persistent_entry() {
+  PersistentKernel k{};
+  const int codes[] = {CODES...};
+  k.ncodes = (int)sizeof...(CODES);
+  for (int i = 0; i < k.ncodes; ++i) k.codes[i] = codes[i];
+  k.fn = reinterpret_cast<const void*>(&persistent_kernel<CODES...>);
+  k.threads = max_threads<CODES...>();
+  k.smem = persistent_tile_bytes<CODES...>();
+  k.tw_smem_per_stage = persistent_tw_bytes_per_stage<CODES...>();
+  return k;
+}
+
+}  // namespace gbfft

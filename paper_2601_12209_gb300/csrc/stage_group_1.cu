@@ -1,0 +1,29 @@
+// Stage-kernel instantiations, group 1: lengths 40, 48, 60, 64, 80.
+// Split across translation units so the library compiles in parallel.
+#include "gbfft_kernels.cuh"
+
+namespace gbfft {
+
+#define GBFFT_STAGE_COMPLEX(L)                           \
+  v.push_back(make_stage_entry<L, -1, kPlain>());        \
+  v.push_back(make_stage_entry<L, 1, kPlain>());         \
+  v.push_back(make_stage_entry<L, -1, kIdentity>());     \
+  v.push_back(make_stage_entry<L, -1, kPoissonZ>());
+#define GBFFT_STAGE_REAL(L)                              \
+  v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
+  v.push_back(make_stage_entry<L, 1, kC2RPre>());
+
+void register_stage_group_1(std::vector<StageKernel>& v) {
+  GBFFT_STAGE_COMPLEX(40)
+  GBFFT_STAGE_REAL(40)
+  GBFFT_STAGE_COMPLEX(48)
+  GBFFT_STAGE_REAL(48)
+  GBFFT_STAGE_COMPLEX(60)
+  GBFFT_STAGE_REAL(60)
+  GBFFT_STAGE_COMPLEX(64)
+  GBFFT_STAGE_REAL(64)
+  GBFFT_STAGE_COMPLEX(80)
+  GBFFT_STAGE_REAL(80)
+}
+
+}  // namespace gbfft

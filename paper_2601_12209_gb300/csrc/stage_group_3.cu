@@ -1,0 +1,25 @@
+// Stage-kernel instantiations, group 3: lengths 192, 240, 256.
+// Split across translation units so the library compiles in parallel.
+#include "gbfft_kernels.cuh"
+
+namespace gbfft {
+
+#define GBFFT_STAGE_COMPLEX(L)                           \
+  v.push_back(make_stage_entry<L, -1, kPlain>());        \
+  v.push_back(make_stage_entry<L, 1, kPlain>());         \
+  v.push_back(make_stage_entry<L, -1, kIdentity>());     \
+  v.push_back(make_stage_entry<L, -1, kPoissonZ>());
+#define GBFFT_STAGE_REAL(L)                              \
+  v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
+  v.push_back(make_stage_entry<L, 1, kC2RPre>());
+
+void register_stage_group_3(std::vector<StageKernel>& v) {
+  GBFFT_STAGE_COMPLEX(192)
+  GBFFT_STAGE_REAL(192)
+  GBFFT_STAGE_COMPLEX(240)
+  GBFFT_STAGE_REAL(240)
+  GBFFT_STAGE_COMPLEX(256)
+  GBFFT_STAGE_REAL(256)
+}
+
+}  // namespace gbfft

@@ -1,0 +1,25 @@
+// Stage-kernel instantiations, group 4: lengths 320, 384, 480.
+// Split across translation units so the library compiles in parallel.
+#include "gbfft_kernels.cuh"
+
+namespace gbfft {
+
+#define GBFFT_STAGE_COMPLEX(L)                           \
+  v.push_back(make_stage_entry<L, -1, kPlain>());        \
+  v.push_back(make_stage_entry<L, 1, kPlain>());         \
+  v.push_back(make_stage_entry<L, -1, kIdentity>());     \
+  v.push_back(make_stage_entry<L, -1, kPoissonZ>());
+#define GBFFT_STAGE_REAL(L)                              \
+  v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
+  v.push_back(make_stage_entry<L, 1, kC2RPre>());
+
+void register_stage_group_4(std::vector<StageKernel>& v) {
+  GBFFT_STAGE_COMPLEX(320)
+  GBFFT_STAGE_REAL(320)
+  GBFFT_STAGE_COMPLEX(384)
+  GBFFT_STAGE_REAL(384)
+  GBFFT_STAGE_COMPLEX(480)
+  GBFFT_STAGE_REAL(480)
+}
+
+}  // namespace gbfft

@@ -1,0 +1,21 @@
+// Stage-kernel instantiations, group 6: lengths 640, 768.
+// Split across translation units so the library compiles in parallel.
+#include "gbfft_kernels.cuh"
+
+namespace gbfft {
+
+#define GBFFT_STAGE_COMPLEX(L)                           \
+  v.push_back(make_stage_entry<L, -1, kPlain>());        \
+  v.push_back(make_stage_entry<L, 1, kPlain>());         \
+  v.push_back(make_stage_entry<L, -1, kIdentity>());     \
+  v.push_back(make_stage_entry<L, -1, kPoissonZ>());
+#define GBFFT_STAGE_REAL(L)                              \
+  v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
+  v.push_back(make_stage_entry<L, 1, kC2RPre>());
+
+void register_stage_group_6(std::vector<StageKernel>& v) {
+  GBFFT_STAGE_COMPLEX(640)
+  GBFFT_STAGE_COMPLEX(768)
+}
+
+}  // namespace gbfft

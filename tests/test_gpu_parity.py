@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Floating point: relative L2 error <= 1e-5 over the whole output (the bound
+stated for FP32 C2C/R2C at 512^3); every error is printed. Index maps: the
+redistribution-alone debug steps must reproduce bit patterns exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_12209_gb300 import _build
+    _build.build()
+    import paper_2601_12209_gb300 as gbmod
+    return gbmod
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def err(name, got, ref):
+    e = oracle.rel_l2(got, ref)
+    print(f"[parity] {name}: rel-L2 {e:.3e}")
+    return e
+
+
+C2C_SHAPES = [  # (nx, ny, nz, batch)
+    (8, 8, 8, 1), (16, 12, 10, 2), (64, 64, 64, 1), (60, 48, 80, 1), (24, 40, 30, 2), (32, 128, 20, 1),
+    (256, 16, 8, 1), (5, 6, 3, 1), (1024, 4, 2, 1), (30, 160, 96, 1),
+]
+
+
+@pytest.mark.parametrize("shape", C2C_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+def test_c2c_forward_inverse(gb, shape, mode):
+    nx, ny, nz, b = shape
+    x = synth.uniform_complex((b, nz, ny, nx), seed=1 + nx + ny + nz)
+    plan = gb.Plan(nx, ny, nz, batch=b, slab=(mode == "slab"), staged=(mode == "pencil_staged"))
+    xd = x.to(dev())
+    X = plan.forward(xd)
+    xr = plan.inverse(X)
+    torch.cuda.synchronize()
+    assert plan.device_error() == 0
+    ref = oracle.fft3(x.numpy())
+    assert err(f"c2c fwd {shape} {mode}", X.cpu().numpy(), ref) < TOL
+    assert err(f"c2c roundtrip {shape} {mode}", xr.cpu().numpy(), x.numpy()) < TOL
+    # inverse alone against the oracle inverse of the same input
+    xi = plan.inverse(xd)
+    assert err(f"c2c inv {shape} {mode}", xi.cpu().numpy(), oracle.ifft3(x.numpy())) < TOL
+    assert torch.equal(xd.cpu(), x)  # input untouched (out-of-place)
+
+
+def test_config1_tiny_c2c_64(gb):
+    """64^3 complex64 uniform[-1,1]: round trip, Parseval, naive DFT on 8x8x8 blocks."""
+    x = synth.uniform_complex((64, 64, 64), seed=1)
+    plan = gb.Plan(64, 64, 64)
+    X = plan.forward(x.to(dev()))
+    xr = plan.inverse(X)
+    Xh = X.cpu().numpy().astype(np.complex128)
+    assert err("cfg1 roundtrip", xr.cpu().numpy(), x.numpy()) < TOL
+    xn = x.numpy().astype(np.complex128)
+    parseval = abs(np.sum(np.abs(Xh) ** 2) / (64 ** 3 * np.sum(np.abs(xn) ** 2)) - 1.0)
+    print(f"[parity] cfg1 Parseval relative deviation {parseval:.3e}")
+    assert parseval < 1e-5
+    bins = [(kx, ky, kz) for kz in range(8) for ky in range(8) for kx in range(8)]
+    off = (37, 21, 50)
+    bins += [((kx + off[0]) % 64, (ky + off[1]) % 64, (kz + off[2]) % 64)
+             for kz in range(8) for ky in range(8) for kx in range(8)]
+    direct = oracle.dft3_bins(xn, bins)
+    got = np.array([Xh[kz, ky, kx] for (kx, ky, kz) in bins])
+    assert err("cfg1 naive DFT 2x8^3 bins", got, direct) < TOL
+    assert err("cfg1 fwd full", Xh, oracle.fft3(xn)) < TOL
+
+
+R2C_SHAPES = [(8, 8, 8, 1), (64, 64, 64, 1), (16, 12, 10, 2), (60, 48, 80, 1), (32, 20, 24, 1), (128, 30, 16, 1),
+              (256, 16, 8, 1)]
+
+
+@pytest.mark.parametrize("shape", R2C_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+def test_r2c_c2r(gb, shape, mode):
+    nx, ny, nz, b = shape
+    r = synth.normal_real((b, nz, ny, nx), seed=2 + nx)
+    plan = gb.Plan(nx, ny, nz, kind="r2c", batch=b, slab=(mode == "slab"), staged=(mode == "pencil_staged"))
+    H = plan.forward(r.to(dev()))
+    r2 = plan.inverse(H)
+    torch.cuda.synchronize()
+    assert plan.device_error() == 0
+    assert err(f"r2c fwd {shape} {mode}", H.cpu().numpy(), oracle.rfft3(r.numpy())) < TOL
+    assert err(f"r2c roundtrip {shape} {mode}", r2.cpu().numpy(), r.numpy()) < TOL
+    # C2R of a NON-Hermitian half spectrum: the Hermitian-projection reading
+    h = synth.uniform_complex((b, nz, ny, nx // 2 + 1), seed=3 + nx)
+    got = plan.inverse(h.to(dev()))
+    assert err(f"c2r non-Hermitian {shape} {mode}", got.cpu().numpy(), oracle.irfft3(h.numpy(), nx)) < TOL
+
+
+@pytest.mark.parametrize("kind", ["c2c", "r2c"])
+@pytest.mark.parametrize("slab", [False, True])
+def test_adjoint_ops(gb, kind, slab):
+    nx, ny, nz = 16, 24, 20
+    plan = gb.Plan(nx, ny, nz, kind=kind, slab=slab)
+    if kind == "c2c":
+        y = synth.uniform_complex((nz, ny, nx), seed=5)
+        a = plan.adjoint(y.to(dev()))
+        assert err("c2c adjoint", a.cpu().numpy(), oracle.c2c_adjoint(y.numpy())) < TOL
+        ia = plan.inverse_adjoint(y.to(dev()))
+        assert err("c2c inverse-adjoint", ia.cpu().numpy(), oracle.c2c_inverse_adjoint(y.numpy())) < TOL
+    else:
+        g = synth.uniform_complex((nz, ny, nx // 2 + 1), seed=6)
+        a = plan.adjoint(g.to(dev()))
+        assert err("r2c adjoint", a.cpu().numpy(), oracle.r2c_adjoint(g.numpy(), nx)) < TOL
+        y = synth.normal_real((nz, ny, nx), seed=7)
+        ia = plan.inverse_adjoint(y.to(dev()))
+        assert err("c2r scaled adjoint", ia.cpu().numpy(), oracle.c2r_scaled_adjoint(y.numpy())) < TOL
+
+
+def test_transposed_out(gb):
+    nx, ny, nz = 32, 24, 16
+    x = synth.uniform_complex((nz, ny, nx), seed=9)
+    plan = gb.Plan(nx, ny, nz, transposed_out=True)
+    C = plan.forward(x.to(dev()))
+    assert C.shape[-3:] == (nx, ny, nz)
+    ref = oracle.layout_a_to_c(oracle.fft3(x.numpy()))
+    assert err("transposed-out fwd", C.cpu().numpy(), ref) < TOL
+    xr = plan.inverse(C)
+    assert err("transposed-out roundtrip", xr.cpu().numpy(), x.numpy()) < TOL
+
+
+# ----------------------------------------------------- index maps (bit-exact)
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (60, 48, 80), (120, 24, 40), (32, 20, 24), (8, 8, 8)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_redistribution_maps_bit_exact(gb, shape):
+    """Debug steps 2/4/6 and 12/14/16 move data only; they must equal the oracle's
+    explicit index maps bit for bit (integer-valued inputs)."""
+    nx, ny, nz = shape
+    plan = gb.Plan(nx, ny, nz)
+    A = synth.integer_complex((nz, ny, nx), seed=11)
+    Ad = A.to(dev())
+    B = torch.empty((nz, nx, ny), dtype=torch.complex64, device=dev())
+    plan.debug_run(2, Ad, B)
+    assert torch.equal(B.cpu(), torch.from_numpy(oracle.layout_a_to_b(A.numpy())))
+    C = torch.empty((nx, ny, nz), dtype=torch.complex64, device=dev())
+    plan.debug_run(4, B, C)
+    assert torch.equal(C.cpu(), torch.from_numpy(oracle.layout_b_to_c(B.cpu().numpy())))
+    N = torch.empty((nz, ny, nx), dtype=torch.complex64, device=dev())
+    plan.debug_run(6, C, N)
+    assert torch.equal(N.cpu(), A)
+    C2 = torch.empty_like(C)
+    plan.debug_run(12, N, C2)
+    assert torch.equal(C2.cpu(), C.cpu())
+    B2 = torch.empty_like(B)
+    plan.debug_run(14, C2, B2)
+    assert torch.equal(B2.cpu(), B.cpu())
+    A2 = torch.empty_like(Ad)
+    plan.debug_run(16, B2, A2)
+    assert torch.equal(A2.cpu(), A)
+
+
+def test_redistribution_maps_r2c_halved_axis(gb):
+    """Same bit-exact check for the y/z redistributions of an R2C plan (nx/2+1 bins)."""
+    nx, ny, nz = 64, 20, 24
+    nxc = nx // 2 + 1
+    plan = gb.Plan(nx, ny, nz, kind="r2c")
+    Bh = synth.integer_complex((nz, nxc, ny), seed=12)
+    C = torch.empty((nxc, ny, nz), dtype=torch.complex64, device=dev())
+    plan.debug_run(4, Bh.to(dev()), C)
+    assert torch.equal(C.cpu(), torch.from_numpy(oracle.layout_b_to_c(Bh.numpy())))
+    N = torch.empty((nz, ny, nxc), dtype=torch.complex64, device=dev())
+    plan.debug_run(6, C, N)
+    assert torch.equal(N.cpu(), torch.from_numpy(oracle.layout_c_to_a(C.cpu().numpy())))
+
+
+@pytest.mark.parametrize("shape", [(32, 24, 20), (60, 48, 16)], ids=lambda s: "x".join(map(str, s)))
+def test_each_stage_alone(gb, shape):
+    """Each FFT stage alone (debug steps 1,3,5,11,13,15) equals the oracle 1D FFT
+    along its axis composed with the stage's layout map."""
+    nx, ny, nz = shape
+    plan = gb.Plan(nx, ny, nz)
+    A = synth.uniform_complex((nz, ny, nx), seed=13)
+    An = A.numpy().astype(np.complex128)
+    B = torch.empty((nz, nx, ny), dtype=torch.complex64, device=dev())
+    plan.debug_run(1, A.to(dev()), B)
+    assert err("stage x", B.cpu().numpy(), oracle.layout_a_to_b(oracle.fft1(An))) < TOL
+    Bn = B.cpu().numpy().astype(np.complex128)
+    C = torch.empty((nx, ny, nz), dtype=torch.complex64, device=dev())
+    plan.debug_run(3, B, C)
+    assert err("stage y", C.cpu().numpy(), oracle.layout_b_to_c(oracle.fft1(Bn))) < TOL
+    Cn = C.cpu().numpy().astype(np.complex128)
+    N = torch.empty((nz, ny, nx), dtype=torch.complex64, device=dev())
+    plan.debug_run(5, C, N)
+    assert err("stage z", N.cpu().numpy(), oracle.layout_c_to_a(oracle.fft1(Cn))) < TOL
+    # inverse steps (unscaled, sign +)
+    C2 = torch.empty_like(C)
+    plan.debug_run(11, A.to(dev()), C2)
+    assert err("stage z inv", C2.cpu().numpy(), oracle.fft1(oracle.layout_a_to_c(An), sign=+1)) < TOL
+    B2 = torch.empty_like(B)
+    plan.debug_run(13, C, B2)
+    # y-inverse on C[x][y][z] along y, written as B[z][x][y]
+    yinv = np.swapaxes(oracle.fft1(np.swapaxes(Cn, -1, -2).copy(), sign=+1), -1, -2)  # [x][y][z]
+    ref = np.transpose(yinv, (2, 0, 1))  # B[z][x][y]
+    assert err("stage y inv", B2.cpu().numpy(), ref) < TOL
+    A2 = torch.empty_like(A.to(dev()))
+    plan.debug_run(15, B, A2)
+    xinv = oracle.fft1(Bn.swapaxes(-1, -2).copy(), sign=+1)  # [z][y][x]
+    assert err("stage x inv", A2.cpu().numpy(), xinv) < TOL
+
+
+def test_persistent_equals_staged_bitwise(gb):
+    """The persistent launch runs the same tile arithmetic as the per-stage launches."""
+    for kind, shape in (("c2c", (64, 64, 64)), ("r2c", (64, 64, 64))):
+        nx, ny, nz = shape
+        x = synth.uniform_complex((nz, ny, nx), seed=21) if kind == "c2c" else synth.normal_real((nz, ny, nx), 22)
+        p1 = gb.Plan(nx, ny, nz, kind=kind)
+        p2 = gb.Plan(nx, ny, nz, kind=kind, staged=True)
+        a = p1.forward(x.to(dev()))
+        b = p2.forward(x.to(dev()))
+        assert torch.equal(a, b)
+        assert torch.equal(p1.inverse(a), p2.inverse(b))
+
+
+def test_device_timeout_is_reported_not_hung(gb):
+    """Dependency waits are bounded: with the debug flag every wait targets one
+    completion too many, times out after ~20 ms, and the error is returned."""
+    plan = gb.Plan(64, 64, 64, debug_timeout=True)
+    x = synth.uniform_complex((64, 64, 64), seed=31).to(dev())
+    plan.forward(x)
+    from paper_2601_12209_gb300 import abi
+    assert plan.device_error() == abi.GBFFT_ERR_TIMEOUT
+    assert plan.device_error() == 0  # read-and-clear
+    ok = gb.Plan(64, 64, 64)
+    X = ok.forward(x)
+    assert err("after timeout", X.cpu().numpy(), oracle.fft3(x.cpu().numpy())) < TOL
+
+
+def test_error_paths(gb):
+    from paper_2601_12209_gb300 import abi
+    plan = gb.Plan(16, 16, 16)
+    x = torch.zeros((16, 16, 16), dtype=torch.complex64, device=dev())
+    with pytest.raises(abi.GbfftError) as e:
+        abi.gbfft_exec(plan.handle, 0, x.data_ptr(), x.data_ptr(), 0)
+    assert e.value.code == abi.GBFFT_ERR_INPLACE
+    y = torch.zeros(16 ** 3 + 2, dtype=torch.complex64, device=dev())
+    with pytest.raises(abi.GbfftError) as e:
+        abi.gbfft_exec(plan.handle, 0, x.data_ptr(), y.data_ptr() + 8, 0)
+    assert e.value.code == abi.GBFFT_ERR_ALIGNMENT
+    with pytest.raises(abi.GbfftError) as e:
+        abi.gbfft_exec(plan.handle, 9, x.data_ptr(), y.data_ptr(), 0)
+    assert e.value.code == abi.GBFFT_ERR_INVALID_ARG
+    with pytest.raises(abi.GbfftError) as e:
+        gb.Plan(14, 16, 16)
+    assert e.value.code == abi.GBFFT_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(abi.GbfftError) as e:
+        abi.gbfft_exec_poisson(plan.handle, x.data_ptr(), y.data_ptr(), 0)
+    assert e.value.code == abi.GBFFT_ERR_INVALID_ARG
+
+
+def test_caller_workspace(gb):
+    plan = gb.Plan(32, 32, 32, kind="r2c")
+    n = plan.workspace_size()
+    assert n >= 2 * 17 * 32 * 32 * 8
+    ws = torch.empty(n, dtype=torch.uint8, device=dev())
+    plan.set_workspace(ws)
+    r = synth.normal_real((32, 32, 32), seed=41)
+    H = plan.forward(r.to(dev()))
+    assert err("r2c with caller workspace", plan.inverse(H).cpu().numpy(), r.numpy()) < TOL
+
+
+def test_exec_host_end_to_end(gb):
+    from paper_2601_12209_gb300 import abi
+    plan = gb.Plan(64, 48, 32)
+    x = synth.uniform_complex((32, 48, 64), seed=51).pin_memory()
+    out = torch.empty_like(x).pin_memory()
+    plan.exec_host(abi.GBFFT_OP_FORWARD, x, out)
+    assert err("exec_host fwd", out.numpy(), oracle.fft3(x.numpy())) < TOL
