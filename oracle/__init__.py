@@ -33,7 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fft_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_LIB_PATH = os.path.join(_HERE, "liboracle-" + __import__("platform").machine() + ".so")
 _lib = None
 _lock = threading.Lock()
 

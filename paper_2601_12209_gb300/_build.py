@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -17,9 +18,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(ROOT, "_build", "gbfft")
+BUILD = os.path.join(ROOT, "_build", "gbfft-" + platform.machine())
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libgbfft.so")
+STAMP = os.path.join(LIBDIR, "libgbfft.machine")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -70,13 +72,17 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         todo.sort(key=lambda p: -os.path.getsize(p[0]))
         with ThreadPoolExecutor(max_workers=workers) as ex:
             list(ex.map(compile_one, todo))
-    if todo or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+    stale_machine = not os.path.exists(STAMP) or open(STAMP).read().strip() != platform.machine()
+    if todo or stale_machine or not os.path.exists(LIB) or \
+            os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link of libgbfft.so failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)
+        with open(STAMP, "w") as fh:
+            fh.write(platform.machine())
         if verbose:
             print(f"[gbfft build] linked {LIB}", file=sys.stderr)
     return LIB
