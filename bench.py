@@ -234,7 +234,13 @@ def main():
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--ncu-case", default=None,
+                    help="run one 512^3 case for a profiler and exit: staged_r2c, persistent_r2c, staged_c2c, "
+                         "persistent_c2c, slab_c2c, slab_r2c")
     args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case(args.ncu_case)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -366,6 +372,23 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def ncu_case(name):
+    """Three forward+inverse pairs of one 512^3 configuration, nothing timed (for ncu)."""
+    import torch
+    import synth
+    import paper_2601_12209_gb300 as gb
+    from paper_2601_12209_gb300 import _build, abi
+    _build.build()
+    kind = "r2c" if name.endswith("r2c") else "c2c"
+    plan = gb.Plan(N, N, N, kind=kind, staged=name.startswith("staged"), slab=name.startswith("slab"))
+    x = (synth.normal_real((N, N, N), seed=2) if kind == "r2c" else synth.uniform_complex((N, N, N), seed=3)).cuda()
+    for _ in range(3):
+        y = plan.exec(abi.GBFFT_OP_FORWARD, x)
+        plan.exec(abi.GBFFT_OP_INVERSE, y)
+    torch.cuda.synchronize()
+    assert plan.device_error() == 0
 
 
 def extra_variants(torch, gb, abi, dev, stream, steps, warmup):

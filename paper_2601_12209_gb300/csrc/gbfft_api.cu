@@ -1,5 +1,5 @@
 // Host side of the C ABI declared in include/gbfft.h: plans, stage
-// descriptors of the pencil and slab pipelines, persistent schedules, kernel
+// descriptors of the pencil and slab pipelines, persistent-launch counters, kernel
 // dispatch.
 #include <cuda_runtime.h>
 
@@ -151,8 +151,6 @@ struct gbfft_plan_s {
   Control* ctl = nullptr;
   unsigned int* counters = nullptr;
   size_t counters_words = 0;
-  unsigned int* sched[kNumPipes] = {nullptr, nullptr, nullptr};
-  unsigned int sched_len[kNumPipes] = {0, 0, 0};
   // end-to-end host path
   void* h_in_dev = nullptr;
   void* h_out_dev = nullptr;
@@ -209,12 +207,8 @@ static void dep(StageDesc& d, int rule, const StageDesc& prev) {
   d.prev_n_gchunks = prev.n_gchunks;
 }
 
-// Tile order of a stage inside a persistent schedule.
-enum TileOrder { kOrderNatural = 0, kOrderGchunkMajor = 1 };
-
 struct Pipeline {
   StageDesc st[kMaxStages];
-  int order[kMaxStages];
   long long in_cap[kMaxStages];   // float2 capacity of the buffer each stage reads
   long long out_cap[kMaxStages];  // ... and writes (-1: unknown, not checked)
   int n = 0;
@@ -262,9 +256,8 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
   const int kx_kind_f = r2c ? kR2CPost : kPlain;
   const int kx_kind_i = r2c ? kC2RPre : kPlain;
   // roles: 0 in, 1 out, 2 W1, 3 W2
-  auto add = [&](const StageDesc& d, int order, int rin, int rout) {
+  auto add = [&](const StageDesc& d, int rin, int rout) {
     P.st[P.n] = d;
-    P.order[P.n] = order;
     P.in_cap[P.n] = cap_of(rin);
     P.out_cap[P.n] = cap_of(rout);
     ++P.n;
@@ -286,9 +279,9 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
         Z = mk(W1, out, nz, kPlain, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nxc, 1,
                (long long)nxc * ny, kCol, scale, 1.f, p->tw_z, nullptr);
       dep(Z, kDepGroup, Y);
-      add(X, kOrderNatural, 0, 1);
-      add(Y, kOrderGchunkMajor, 1, 2);
-      add(Z, kOrderNatural, 2, 1);
+      add(X, 0, 1);
+      add(Y, 1, 2);
+      add(Z, 2, 1);
     } else {
       StageDesc X = mk(in, out, Lx, kx_kind_f, -1, B, nz, ny, NA, (long long)rowA * ny, rowA, 1, kRow, Nc,
                        (long long)nxc * ny, nxc, 1, kRow, 1.f, r2c ? interior : 1.f, p->tw_x, p->tw2);
@@ -298,9 +291,9 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       StageDesc Z = mk(out, out, nz, kPlain, -1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nxc, 1,
                        (long long)nxc * ny, kCol, scale, 1.f, p->tw_z, nullptr);
       dep(Z, kDepSameGchunk, Y);
-      add(X, kOrderNatural, 0, 1);
-      add(Y, kOrderNatural, 1, 1);
-      add(Z, kOrderNatural, 1, 1);
+      add(X, 0, 1);
+      add(Y, 1, 1);
+      add(Z, 1, 1);
     }
   } else if (pipe == kPipeInv) {
     const float interior = (op == GBFFT_OP_ADJOINT) ? 0.5f : 1.f;
@@ -321,9 +314,9 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       StageDesc X = mk(Bb, out, Lx, kx_kind_i, +1, B, nz, ny, Nc, (long long)nxc * ny, 1, ny, kCol, NA,
                        (long long)rowA * ny, rowA, 1, kRow, scale, r2c ? interior : 1.f, p->tw_x, p->tw2);
       dep(X, kDepGchunkOfOuter, Y);
-      add(Z, kOrderNatural, 0, r2c ? 2 : 1);
-      add(Y, kOrderGchunkMajor, r2c ? 2 : 1, r2c ? 3 : 2);
-      add(X, kOrderNatural, r2c ? 3 : 2, 1);
+      add(Z, 0, r2c ? 2 : 1);
+      add(Y, r2c ? 2 : 1, r2c ? 3 : 2);
+      add(X, r2c ? 3 : 2, 1);
     } else {
       void* D = r2c ? W1 : out;
       StageDesc Z = mk(in, D, nz, kPlain, +1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nxc, 1,
@@ -334,9 +327,9 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       StageDesc X = mk(D, out, Lx, kx_kind_i, +1, B, nz, ny, Nc, (long long)nxc * ny, nxc, 1, kRow, NA,
                        (long long)rowA * ny, rowA, 1, kRow, scale, r2c ? interior : 1.f, p->tw_x, p->tw2);
       dep(X, kDepOuter, Y);
-      add(Z, kOrderGchunkMajor, 0, r2c ? 2 : 1);
-      add(Y, kOrderNatural, r2c ? 2 : 1, r2c ? 2 : 1);
-      add(X, kOrderNatural, r2c ? 2 : 1, 1);
+      add(Z, 0, r2c ? 2 : 1);
+      add(Y, r2c ? 2 : 1, r2c ? 2 : 1);
+      add(X, r2c ? 2 : 1, 1);
     }
   } else {  // Poisson (R2C plans)
     const int M = Lx;
@@ -357,11 +350,11 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       StageDesc Xi = mk(W1, out, M, kC2RPre, +1, B, nz, ny, Nc, (long long)nxc * ny, 1, ny, kCol, NA,
                         (long long)M * ny, M, 1, kRow, 1.f, 1.f, p->tw_x, p->tw2);
       dep(Xi, kDepGchunkOfOuter, Yi);
-      add(X, kOrderNatural, 0, 2);
-      add(Y, kOrderGchunkMajor, 2, 3);
-      add(PZ, kOrderNatural, 3, 3);
-      add(Yi, kOrderGchunkMajor, 3, 2);
-      add(Xi, kOrderNatural, 2, 1);
+      add(X, 0, 2);
+      add(Y, 2, 3);
+      add(PZ, 3, 3);
+      add(Yi, 3, 2);
+      add(Xi, 2, 1);
     } else {
       StageDesc X = mk(in, W1, M, kR2CPost, -1, B, nz, ny, NA, (long long)M * ny, M, 1, kRow, Nc,
                        (long long)nxc * ny, nxc, 1, kRow, 1.f, 1.f, p->tw_x, p->tw2);
@@ -379,11 +372,11 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       StageDesc Xi = mk(W1, out, M, kC2RPre, +1, B, nz, ny, Nc, (long long)nxc * ny, nxc, 1, kRow, NA,
                         (long long)M * ny, M, 1, kRow, 1.f, 1.f, p->tw_x, p->tw2);
       dep(Xi, kDepOuter, Yi);
-      add(X, kOrderNatural, 0, 2);
-      add(Y, kOrderNatural, 2, 2);
-      add(PZ, kOrderGchunkMajor, 2, 2);
-      add(Yi, kOrderNatural, 2, 2);
-      add(Xi, kOrderNatural, 2, 1);
+      add(X, 0, 2);
+      add(Y, 2, 2);
+      add(PZ, 2, 2);
+      add(Yi, 2, 2);
+      add(Xi, 2, 1);
     }
   }
   return P;
@@ -395,31 +388,16 @@ static int pipe_of(int op) {
   return kPipePoisson;
 }
 
-// Ticket list of a persistent launch: stage by stage, each stage's tiles in
-// the order that lets it start as early as its dependency rule allows.
-static std::vector<unsigned int> build_schedule(const Pipeline& P) {
-  std::vector<unsigned int> s;
-  for (int k = 0; k < P.n; ++k) {
-    const StageDesc& d = P.st[k];
-    const unsigned int tag = (unsigned int)k << 28;
-    if (P.order[k] == kOrderNatural) {
-      for (long long t = 0; t < d.n_tiles; ++t) s.push_back(tag | (unsigned int)t);
-    } else {
-      for (int b = 0; b < d.batch; ++b)
-        for (int gc = 0; gc < d.n_gchunks; ++gc)
-          for (int o = 0; o < d.n_outer; ++o)
-            s.push_back(tag | (unsigned int)(((long long)b * d.n_outer + o) * d.n_gchunks + gc));
-    }
-  }
-  return s;
+// Counters of one stage: per (batch, outer), per (batch, outer/16), per
+// (batch, group chunk), per batch, and one for the whole stage.
+static size_t stage_counter_words(const StageDesc& d) {
+  return (size_t)d.batch * d.n_outer + (size_t)d.batch * gchunks(d.n_outer) + (size_t)d.batch * d.n_gchunks +
+         (size_t)d.batch + 1;
 }
 
 static size_t counter_words(const Pipeline& P) {
   size_t w = 0;
-  for (int k = 0; k < P.n; ++k) {
-    const StageDesc& d = P.st[k];
-    w += (size_t)d.batch * d.n_outer + (size_t)d.batch * d.n_gchunks + (size_t)d.batch;
-  }
+  for (int k = 0; k < P.n; ++k) w += stage_counter_words(P.st[k]);
   return w;
 }
 
@@ -503,18 +481,24 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
   std::memset(&a, 0, sizeof(a));
   a.nstages = P.n;
   for (int s = 0; s < P.n; ++s) a.st[s] = P.st[s];
-  a.sched = p->sched[pipe];
-  a.total = p->sched_len[pipe];
+  long long total = 0;
+  for (int s = 0; s < P.n; ++s) total += P.st[s].n_tiles;
+  if (total >= (1LL << 31)) return GBFFT_ERR_INVALID_ARG;
+  a.total = (unsigned int)total;
   a.ctl = p->ctl;
   unsigned int* c = p->counters;
   for (int s = 0; s < P.n; ++s) {
     const StageDesc& d = P.st[s];
     a.cnt_outer[s] = c;
     c += (size_t)d.batch * d.n_outer;
+    a.cnt_outer16[s] = c;
+    c += (size_t)d.batch * gchunks(d.n_outer);
     a.cnt_gchunk[s] = c;
     c += (size_t)d.batch * d.n_gchunks;
     a.cnt_total[s] = c;
     c += (size_t)d.batch;
+    a.cnt_stage[s] = c;
+    c += 1;
   }
   const bool dbg = (p->flags & GBFFT_DEBUG_TIMEOUT) != 0;
   a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
@@ -561,7 +545,6 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->tw2);
   if (p->ws_owned) cudaFree(p->ws);
   cudaFree(p->ctl);
-  for (int i = 0; i < kNumPipes; ++i) cudaFree(p->sched[i]);
   cudaFree(p->h_in_dev);
   cudaFree(p->h_out_dev);
   if (p->h_stream) cudaStreamDestroy(p->h_stream);
@@ -661,11 +644,11 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   p->rowA = Lx;  // complex values per input row (real pairs for R2C)
   p->Nc = (long long)p->nxc * ny * nz;
   p->NA = (long long)p->rowA * ny * nz;
-  // tiles are indexed with 28 bits in the persistent schedule
+  // tickets of a persistent launch are 32-bit
   if ((long long)batch * std::max<long long>((long long)nz * gchunks(ny),
                                              std::max<long long>((long long)p->nxc * gchunks(nz),
                                                                  (long long)ny * gchunks(p->nxc))) >=
-      (1LL << 28)) {
+      (1LL << 29)) {
     delete p;
     return GBFFT_ERR_INVALID_ARG;
   }
@@ -683,22 +666,14 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
     ok = p->tw2 != nullptr;
   }
-  // persistent schedules and counters
+  // persistent-launch counters: sized for the largest pipeline
   size_t words = 0;
   for (int pipe = 0; pipe < kNumPipes && ok; ++pipe) {
     if (pipe == kPipePoisson && kind != GBFFT_R2C) continue;
     int op = pipe == kPipeFwd ? GBFFT_OP_FORWARD : (pipe == kPipeInv ? GBFFT_OP_INVERSE : 4);
     const Buf none{nullptr, -1};
     Pipeline P = build_pipeline(p, pipe, op, none, none, none, none);
-    std::vector<unsigned int> s = build_schedule(P);
     words = std::max(words, counter_words(P));
-    if (cudaMalloc(&p->sched[pipe], s.size() * sizeof(unsigned int)) != cudaSuccess ||
-        cudaMemcpy(p->sched[pipe], s.data(), s.size() * sizeof(unsigned int), cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
-      ok = false;
-      break;
-    }
-    p->sched_len[pipe] = (unsigned int)s.size();
   }
   if (ok) {
     p->counters_words = words;

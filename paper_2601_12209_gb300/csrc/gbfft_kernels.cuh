@@ -65,24 +65,26 @@ StageKernel make_stage_entry() {
 //
 // The paper's dynamic scheduler hands ready DTasks to idle workers
 // (Sections III-C, IV-C/D). Here every block is a worker: it takes the next
-// ticket from one atomic counter, looks the ticket up in a host-built
-// schedule (stage, tile) in an order where every dependency comes earlier,
-// waits (bounded) until the tiles it reads are complete, runs the tile, and
-// publishes its completion on per-outer, per-group-chunk and per-batch
+// ticket from one atomic counter (tickets are the stages' tiles, stage after
+// stage, so every dependency has a smaller ticket), waits (bounded) until the
+// tiles it reads are complete, runs the tile, and publishes its completion on
 // counters -- the per-chunk dependency tracking of DataDepsTaskQueue
-// (Section IV-D) with counters instead of task graphs.
+// (Section IV-D) with counters instead of task graphs. Each worker fetches
+// its next ticket while it works on the current one, and stops checking a
+// stage's dependencies once the whole producer stage is known complete.
 
 struct PersistentArgs {
   StageDesc st[kMaxStages];
   int nstages;
-  const unsigned int* sched;   // ticket -> (stage << 28) | tile
-  unsigned int total;          // tickets
+  unsigned int total;                    // tickets = sum of the stages' tiles
   Control* ctl;
-  unsigned int* cnt_outer[kMaxStages];
-  unsigned int* cnt_gchunk[kMaxStages];
-  unsigned int* cnt_total[kMaxStages];
-  long long timeout_ns;        // bound on every dependency wait
-  int debug_never;             // wait for one more completion than exists (timeout test)
+  unsigned int* cnt_outer[kMaxStages];   // per (batch, outer index)
+  unsigned int* cnt_outer16[kMaxStages]; // per (batch, outer index / 16)
+  unsigned int* cnt_gchunk[kMaxStages];  // per (batch, group chunk)
+  unsigned int* cnt_total[kMaxStages];   // per batch entry
+  unsigned int* cnt_stage[kMaxStages];   // one per stage
+  long long timeout_ns;                  // bound on every dependency wait
+  int debug_never;                       // wait for one more completion than exists (timeout test)
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -102,34 +104,39 @@ __device__ __forceinline__ bool wait_counter(const unsigned int* p, unsigned int
                                              unsigned long long t0) {
   unsigned int spins = 0;
   while (ld_acquire(p) < target) {
-    if ((++spins & 63) == 0) {
+    if ((++spins & 15) == 0) {
       if (*reinterpret_cast<volatile int*>(&a.ctl->abort)) return false;
       if ((long long)(global_ns() - t0) > a.timeout_ns) return false;
     }
-    __nanosleep(64);
+    __nanosleep(100);
   }
   return true;
 }
 
 // Wait for the producer tiles (previous stage) that tile `tile` of stage s reads.
-__device__ __forceinline__ bool wait_deps(const PersistentArgs& a, int s, long long tile) {
+// One counter per rule; `complete` caches "the whole previous stage is done".
+__device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDesc* st, int* complete, int s,
+                                          long long tile) {
   if (s == 0) return true;
-  const StageDesc& d = a.st[s];
-  if (d.dep_rule == kDepNone) return true;
+  const StageDesc& d = st[s];
+  if (d.dep_rule == kDepNone || complete[s - 1]) return true;
+  const unsigned int extra = a.debug_never ? 1u : 0u;
+  if (ld_acquire(a.cnt_stage[s - 1]) >= (unsigned int)st[s - 1].n_tiles + extra) {
+    complete[s - 1] = 1;
+    return true;
+  }
   const long long gc = tile % d.n_gchunks;
   const long long rest = tile / d.n_gchunks;
   const int o = (int)(rest % d.n_outer);
   const int b = (int)(rest / d.n_outer);
-  const unsigned int extra = a.debug_never ? 1u : 0u;
   const unsigned long long t0 = global_ns();
   switch (d.dep_rule) {
     case kDepGroup: {
-      const int g0 = (int)gc * kTileP;
-      const int valid = min(kTileP, d.n_group - g0);
-      const unsigned int target = (unsigned int)d.prev_n_gchunks + extra;
-      for (int g = g0; g < g0 + valid; ++g)
-        if (!wait_counter(a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + g, target, a, t0)) return false;
-      return true;
+      // the consumer's group chunk gc is the producer's outer chunk gc
+      const int n16 = (d.prev_n_outer + kTileP - 1) / kTileP;
+      const int outers = min(kTileP, d.prev_n_outer - (int)gc * kTileP);
+      return wait_counter(a.cnt_outer16[s - 1] + (long long)b * n16 + gc,
+                          (unsigned int)(outers * d.prev_n_gchunks) + extra, a, t0);
     }
     case kDepOuter:
       return wait_counter(a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + o,
@@ -141,22 +148,28 @@ __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, int s, long l
       return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + gc,
                           (unsigned int)d.prev_n_outer + extra, a, t0);
     case kDepAll:
-      return wait_counter(a.cnt_total[s - 1] + b,
-                          (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra, a, t0);
+      return wait_counter(a.cnt_total[s - 1] + b, (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra, a,
+                          t0);
   }
   return true;
 }
 
-__device__ __forceinline__ void signal_done(const PersistentArgs& a, int s, long long tile) {
-  const StageDesc& d = a.st[s];
+// Publish a finished tile. Called by one thread after a block barrier: the
+// fence orders the whole block's stores (observed through the barrier) before
+// the counter updates that consumers acquire.
+__device__ __forceinline__ void signal_done(const PersistentArgs& a, const StageDesc* st, int s, long long tile) {
+  const StageDesc& d = st[s];
   const long long gc = tile % d.n_gchunks;
   const long long rest = tile / d.n_gchunks;
   const int o = (int)(rest % d.n_outer);
   const int b = (int)(rest / d.n_outer);
+  const int n16 = (d.n_outer + kTileP - 1) / kTileP;
   __threadfence();
   atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);
+  atomicAdd(a.cnt_outer16[s] + (long long)b * n16 + o / kTileP, 1u);
   atomicAdd(a.cnt_gchunk[s] + (long long)b * d.n_gchunks + gc, 1u);
   atomicAdd(a.cnt_total[s] + b, 1u);
+  atomicAdd(a.cnt_stage[s], 1u);
 }
 
 // Runtime dispatch of one tile over the compile-time list of (L, kind, dir)
@@ -179,9 +192,18 @@ __host__ __device__ constexpr int max_len() {
 }
 
 template <int CODE, int... REST>
-__host__ __device__ constexpr int max_threads() {
+__host__ __device__ constexpr int min_threads() {
   if constexpr (sizeof...(REST) == 0) return threads_for(CODE >> 8);
-  else return threads_for(CODE >> 8) > max_threads<REST...>() ? threads_for(CODE >> 8) : max_threads<REST...>();
+  else return threads_for(CODE >> 8) < min_threads<REST...>() ? threads_for(CODE >> 8) : min_threads<REST...>();
+}
+
+// Block size of a persistent family: the smallest natural block size of its
+// lengths, so the register budget of the longest length is not cut down to
+// what twice as many threads would allow (the longer stages then run more
+// butterflies per thread).
+template <int... CODES>
+__host__ __device__ constexpr int family_threads() {
+  return min_threads<CODES...>();
 }
 
 // Shared memory of a persistent launch: the tile, then one twiddle block
@@ -200,48 +222,67 @@ __device__ __forceinline__ int stage_code(const StageDesc& d) {
 }
 
 template <int... CODES>
-__global__ void __launch_bounds__(max_threads<CODES...>(), min_blocks_for(max_len<CODES...>()))
+__global__ void __launch_bounds__(family_threads<CODES...>(), min_blocks_for(max_len<CODES...>()))
 persistent_kernel(PersistentArgs a) {
-  constexpr int THREADS = max_threads<CODES...>();
+  constexpr int THREADS = family_threads<CODES...>();
   constexpr int LM = max_len<CODES...>();
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* tws = sm + (LM + 1) * kTileP;
+  __shared__ StageDesc s_st[kMaxStages];
+  __shared__ unsigned int s_first[kMaxStages + 1];
+  __shared__ int s_complete[kMaxStages];
   __shared__ unsigned int s_ticket;
   __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    unsigned int acc = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxStages; ++k) {
+      s_st[k] = a.st[k];
+      s_first[k] = acc;
+      s_complete[k] = 0;
+      if (k < a.nstages) acc += (unsigned int)a.st[k].n_tiles;
+    }
+    s_first[kMaxStages] = acc;
+    s_ticket = atomicAdd(&a.ctl->ticket, 1u);
+  }
+  __syncthreads();
   for (int s = 0; s < a.nstages; ++s) {
     float2* tw = tws + s * (2 * LM + 1);
-    const StageDesc& d = a.st[s];
+    const StageDesc& d = s_st[s];
     for (int i = threadIdx.x; i < d.L; i += THREADS) tw[i] = d.tw[i];
     if (d.kind == kR2CPost || d.kind == kC2RPre)
       for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[LM + i] = d.tw2[i];
   }
   __syncthreads();
+  unsigned int next = 0;
   for (;;) {
+    const unsigned int t = s_ticket;
+    if (t >= a.total) break;
+    int s = 0;
+    while (s + 1 < a.nstages && t >= s_first[s + 1]) ++s;
+    const long long tile = (long long)(t - s_first[s]);
     if (threadIdx.x == 0) {
-      s_ticket = atomicAdd(&a.ctl->ticket, 1u);
-      s_ok = *reinterpret_cast<volatile int*>(&a.ctl->abort) ? 0 : 1;
-      if (s_ok && s_ticket < a.total) {
-        const unsigned int e = a.sched[s_ticket];
-        if (!wait_deps(a, (int)(e >> 28), (long long)(e & 0x0FFFFFFFu))) {
-          atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
-          atomicExch(&a.ctl->abort, 1);
-          s_ok = 0;
-        }
+      next = atomicAdd(&a.ctl->ticket, 1u);  // prefetch: the result is needed after the tile
+      int ok = *reinterpret_cast<volatile int*>(&a.ctl->abort) ? 0 : 1;
+      if (ok && !wait_deps(a, s_st, s_complete, s, tile)) {
+        atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
+        atomicExch(&a.ctl->abort, 1);
+        ok = 0;
       }
+      s_ok = ok;
     }
     __syncthreads();
-    const unsigned int t = s_ticket;
-    if (t >= a.total || !s_ok) break;
-    const unsigned int e = a.sched[t];
-    const int s = (int)(e >> 28);
-    const long long tile = (long long)(e & 0x0FFFFFFFu);
-    const StageDesc& d = a.st[s];
+    if (!s_ok) break;
+    const StageDesc& d = s_st[s];
     const float2* tw = tws + s * (2 * LM + 1);
     dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile, sm, tw, tw + LM);
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) signal_done(a, s, tile);
+    if (threadIdx.x == 0) {
+      signal_done(a, s_st, s, tile);
+      s_ticket = next;
+    }
+    __syncthreads();
   }
 }
 
@@ -252,7 +293,7 @@ PersistentKernel make_persistent_entry() {
   k.ncodes = (int)sizeof...(CODES);
   for (int i = 0; i < k.ncodes; ++i) k.codes[i] = codes[i];
   k.fn = reinterpret_cast<const void*>(&persistent_kernel<CODES...>);
-  k.threads = max_threads<CODES...>();
+  k.threads = family_threads<CODES...>();
   k.smem = persistent_tile_bytes<CODES...>();
   k.tw_smem_per_stage = persistent_tw_bytes_per_stage<CODES...>();
   return k;

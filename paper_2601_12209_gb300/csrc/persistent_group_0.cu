@@ -1,11 +1,12 @@
 // Persistent-kernel families for cubic complex-to-complex grids: one kernel
-// per length serves the forward (x, y, z) and inverse (z, y, x) launches.
+// per length and direction (forward: x, y, z stages; inverse: z, y, x).
 #include "gbfft_kernels.cuh"
 
 namespace gbfft {
 
-#define GBFFT_C2C_FAMILY(L) \
-  v.push_back(make_persistent_entry<kcode(L, kPlain, -1), kcode(L, kPlain, 1)>());
+#define GBFFT_C2C_FAMILY(L)                                             \
+  v.push_back(make_persistent_entry<kcode(L, kPlain, -1)>());           \
+  v.push_back(make_persistent_entry<kcode(L, kPlain, 1)>());
 
 void register_persistent_group_0(std::vector<PersistentKernel>& v) {
   GBFFT_C2C_FAMILY(64)
