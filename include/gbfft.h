@@ -83,6 +83,7 @@ typedef struct gbfft_plan_s* gbfft_plan;
 #define GBFFT_ERR_CUDA (-6)             /* a CUDA runtime call failed */
 #define GBFFT_ERR_TIMEOUT (-7)          /* a device dependency wait ran out of time */
 #define GBFFT_ERR_NO_DEVICE (-8)        /* no CUDA device */
+#define GBFFT_ERR_STATIC_LIMIT (-9)     /* grid larger than GBFFT_NOALLOC_MAX_POINTS */
 
 /*
  * Create a plan for `batch` grids of nx x ny x nz (Section V-B: a reusable
@@ -166,6 +167,35 @@ int gbfft_get_device_error(gbfft_plan plan, int* code);
  * pure moves and reproduce bit patterns exactly.
  */
 int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* stream);
+
+/*
+ * Allocation-free C2C transform (the paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory when they run
+ * the transform -- for example code that runs while a CUDA graph is being
+ * captured, or code whose device memory belongs to a pool or framework
+ * allocator that forbids side allocations). It needs no plan and calls no
+ * cudaMalloc, cudaFree or other allocating routine: the intermediate stage
+ * array lives in a file-scope static __device__ buffer of
+ * GBFFT_NOALLOC_MAX_POINTS complex64 values (32 MiB) that every GPU which
+ * loads this library holds until the process exits, and the twiddle tables
+ * of every supported length sit in a second static array.
+ *   nx, ny, nz : one grid, nx*ny*nz <= GBFFT_NOALLOC_MAX_POINTS (else
+ *                GBFFT_ERR_STATIC_LIMIT, nothing launched); every length must
+ *                satisfy gbfft_supported_length and be <= 1024
+ *   op         : GBFFT_OP_FORWARD / INVERSE / ADJOINT / INVERSE_ADJOINT
+ *   in, out    : caller-owned device buffers, complex64 [nz][ny][nx],
+ *                16-byte aligned, distinct; in is not written
+ *   stream     : cudaStream_t; the call enqueues three stage launches (the
+ *                pencil x, y, z stages) and returns without waiting
+ * The first call on a device sets that device up (resolves the static
+ * arrays' device addresses, uploads the twiddle tables with a synchronous
+ * copy); make that first call before any stream capture. Every call shares
+ * the one scratch buffer: calls that overlap on the GPU (different streams,
+ * or concurrent host threads) race on it. Nothing in it needs to start at
+ * zero -- each stage writes every element before the next reads it.
+ */
+#define GBFFT_NOALLOC_MAX_POINTS 4194304
+int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void* in, void* out, void* stream);
 
 /* Human-readable name of an error code (static storage). */
 const char* gbfft_strerror(int code);

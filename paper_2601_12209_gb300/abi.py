@@ -36,6 +36,8 @@ GBFFT_ERR_ALLOC = -5
 GBFFT_ERR_CUDA = -6
 GBFFT_ERR_TIMEOUT = -7
 GBFFT_ERR_NO_DEVICE = -8
+GBFFT_ERR_STATIC_LIMIT = -9
+GBFFT_NOALLOC_MAX_POINTS = 4194304
 
 # every symbol include/gbfft.h declares
 EXPORTED = (
@@ -43,7 +45,7 @@ EXPORTED = (
     "gbfft_exec_forward", "gbfft_exec_inverse", "gbfft_exec_adjoint", "gbfft_exec_inverse_adjoint",
     "gbfft_exec_poisson", "gbfft_exec_host", "gbfft_workspace_size", "gbfft_set_workspace",
     "gbfft_get_device_error", "gbfft_debug_run", "gbfft_strerror", "gbfft_plan_destroy",
-    "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version",
+    "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version", "gbfft_exec_c2c_noalloc",
 )
 
 _lib = None
@@ -88,6 +90,7 @@ def load() -> ctypes.CDLL:
             "gbfft_supported_length": (i, [i]),
             "gbfft_radix_plan": (i, [i, ctypes.POINTER(i), i]),
             "gbfft_version": (ctypes.c_char_p, []),
+            "gbfft_exec_c2c_noalloc": (i, [i, i, i, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -199,6 +202,12 @@ def gbfft_get_device_error(plan: int) -> int:
 def gbfft_debug_run(plan: int, step: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
     _call("gbfft_debug_run", ctypes.c_void_p(plan), int(step), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
           ctypes.c_void_p(stream))
+
+
+def gbfft_exec_c2c_noalloc(nx: int, ny: int, nz: int, op: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    """Allocation-free C2C transform on one grid; see include/gbfft.h."""
+    _call("gbfft_exec_c2c_noalloc", int(nx), int(ny), int(nz), int(op), ctypes.c_void_p(in_ptr),
+          ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
 
 
 def raw_rc(name: str, *args) -> int:

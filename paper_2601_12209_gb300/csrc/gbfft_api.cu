@@ -430,6 +430,12 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream) {
   return cuda_err(e);
 }
 
+namespace gbfft {
+// Launch one stage through the registry; used by the allocation-free entry
+// point in gbfft_static.cu.
+int launch_stage_external(const StageDesc& d, cudaStream_t stream) { return launch_stage(d, stream); }
+}  // namespace gbfft
+
 static int ensure_workspace(gbfft_plan_s* p) {
   if (p->n_ws == 0 || p->ws) return GBFFT_OK;
   size_t need = 0;
@@ -577,6 +583,8 @@ const char* gbfft_strerror(int code) {
       return "device dependency wait timed out";
     case GBFFT_ERR_NO_DEVICE:
       return "no CUDA device";
+    case GBFFT_ERR_STATIC_LIMIT:
+      return "grid larger than the static scratch of gbfft_exec_c2c_noalloc";
     default:
       return "unknown error";
   }
