@@ -418,10 +418,18 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
     med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_ADJOINT], steps, warmup, stream)
     out["r2c_512_fwd_adjoint_ms"] = med[0] + med[1]
     p.close()
-    ps = gb.Plan(N, N, N, kind="r2c", staged=True)
-    med, _ = time_variant(torch, ps, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
-    out["r2c_512_pencil_staged_fwd_inv_ms"] = med[0] + med[1]
-    ps.close()
+    for tma in (True, False):
+        ps = gb.Plan(N, N, N, kind="r2c", staged=True, tma=tma)
+        med, _ = time_variant(torch, ps, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+        out["r2c_512_pencil_staged_" + ("tma" if tma else "lsu") + "_fwd_inv_ms"] = med[0] + med[1]
+        ps.close()
+    x = synth.uniform_complex((N, N, N), seed=3).to(dev)
+    for tma in (True, False):
+        ps = gb.Plan(N, N, N, staged=True, tma=tma)
+        med, _ = time_variant(torch, ps, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+        out["c2c_512_pencil_staged_" + ("tma" if tma else "lsu") + "_fwd_inv_ms"] = med[0] + med[1]
+        ps.close()
+    del x
     # cuFFT via torch.fft on the same GPU: context only, not a target
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(warmup):

@@ -62,6 +62,7 @@ typedef struct gbfft_plan_s* gbfft_plan;
 #define GBFFT_TRANSPOSED_OUT 2u  /* pencil only: forward leaves C[b][kx][ky][kz] ("collect from C",
                                     Algorithm 1); inverse then reads that layout */
 #define GBFFT_STAGED 4u          /* one launch per stage instead of one persistent launch */
+#define GBFFT_NO_TMA 8u          /* staged launches load tiles with thread loads instead of tensor copies */
 #define GBFFT_DEBUG_TIMEOUT (1u << 16) /* tests only: every dependency wait of the persistent launch
                                           waits for one completion too many and times out after
                                           ~20 ms; gbfft_get_device_error then returns
@@ -91,7 +92,7 @@ typedef struct gbfft_plan_s* gbfft_plan;
  *   kind  : GBFFT_C2C or GBFFT_R2C (R2C needs even nx)
  *   dtype : GBFFT_FP32
  *   flags : GBFFT_PENCIL or GBFFT_SLAB, optionally | GBFFT_TRANSPOSED_OUT
- *           (pencil only) | GBFFT_STAGED | GBFFT_DEBUG_TIMEOUT
+ *           (pencil only) | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT
  * Every axis length (nx/2 for the R2C x axis) must satisfy
  * gbfft_supported_length. Uses the current CUDA device; allocates twiddle
  * tables and schedules (and the workspace lazily, on first exec).

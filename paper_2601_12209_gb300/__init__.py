@@ -48,19 +48,21 @@ class Plan:
 
     kind: "c2c" or "r2c"; slab: plane-wise x,y then z (else pencil);
     transposed_out: pencil forward output left as [b][kx][ky][kz];
-    staged: one launch per stage instead of the persistent launch.
+    staged: one launch per stage instead of the persistent launch;
+    tma=False: staged launches load tiles with thread loads instead of tensor copies.
     """
 
     def __init__(self, nx: int, ny: int, nz: int, kind: str = "c2c", batch: int = 1, slab: bool = False,
                  transposed_out: bool = False, staged: bool = False, debug_timeout: bool = False,
-                 cached: bool = False):
+                 cached: bool = False, tma: bool = True):
         self.nx, self.ny, self.nz, self.batch = int(nx), int(ny), int(nz), int(batch)
         self.kind = kind
         k = GBFFT_R2C if kind == "r2c" else GBFFT_C2C
         if kind not in ("c2c", "r2c"):
             raise ValueError("kind must be 'c2c' or 'r2c'")
         flags = (abi.GBFFT_SLAB if slab else 0) | (abi.GBFFT_TRANSPOSED_OUT if transposed_out else 0) | \
-                (abi.GBFFT_STAGED if staged else 0) | (abi.GBFFT_DEBUG_TIMEOUT if debug_timeout else 0)
+                (abi.GBFFT_STAGED if staged else 0) | (abi.GBFFT_DEBUG_TIMEOUT if debug_timeout else 0) | \
+                (0 if tma else abi.GBFFT_NO_TMA)
         self.flags = flags
         self.transposed_out = transposed_out
         self._cached = cached

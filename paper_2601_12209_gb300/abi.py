@@ -21,6 +21,7 @@ GBFFT_PENCIL = 0
 GBFFT_SLAB = 1
 GBFFT_TRANSPOSED_OUT = 2
 GBFFT_STAGED = 4
+GBFFT_NO_TMA = 8
 GBFFT_DEBUG_TIMEOUT = 1 << 16
 GBFFT_OP_FORWARD = 0
 GBFFT_OP_INVERSE = 1

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/gbfft.h: plans, stage
 // descriptors of the pencil and slab pipelines, persistent-launch counters, kernel
 // dispatch.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +28,9 @@ void register_stage_group_6(std::vector<StageKernel>&);
 void register_stage_group_7(std::vector<StageKernel>&);
 void register_persistent_group_0(std::vector<PersistentKernel>&);
 void register_persistent_group_1(std::vector<PersistentKernel>&);
+void register_tma_group_0(std::vector<TmaKernel>&);
+void register_tma_group_1(std::vector<TmaKernel>&);
+void register_tma_group_2(std::vector<TmaKernel>&);
 
 std::vector<StageKernel>& stage_registry() {
   static std::vector<StageKernel> v;
@@ -34,6 +38,10 @@ std::vector<StageKernel>& stage_registry() {
 }
 std::vector<PersistentKernel>& persistent_registry() {
   static std::vector<PersistentKernel> v;
+  return v;
+}
+std::vector<TmaKernel>& tma_registry() {
+  static std::vector<TmaKernel> v;
   return v;
 }
 
@@ -52,6 +60,10 @@ static void ensure_registry() {
     auto& p = persistent_registry();
     register_persistent_group_0(p);
     register_persistent_group_1(p);
+    auto& t = tma_registry();
+    register_tma_group_0(t);
+    register_tma_group_1(t);
+    register_tma_group_2(t);
   });
 }
 
@@ -91,6 +103,77 @@ static const StageKernel* find_stage(int L, int dir, int kind) {
 }
 
 static bool stage_supported(int L) { return find_stage(L, -1, kPlain) != nullptr; }
+
+static const TmaKernel* find_tma(int L, int dir, int kind, int src) {
+  ensure_registry();
+  for (const auto& k : tma_registry())
+    if (k.L == L && k.dir == dir && k.kind == kind && k.src == src) return &k;
+  return nullptr;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the CUDA runtime).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of a stage's input for the TMA kernel, or false when the layout
+// cannot be described (a stride or the base not a multiple of 16 bytes).
+//   row side:    dims {2 n_in floats, pencils, outer, batch}, box {32, 16, 1, 1}
+//   column side: dims {2 pencils floats, n_in, outer, batch}, box {32, 32, 1, 1}
+static bool encode_input_map(const StageDesc& d, int src, CUtensorMap* m) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  if ((reinterpret_cast<uintptr_t>(d.in) & 15) != 0) return false;
+  cuuint64_t dims[4];
+  long long strides_el[3];
+  cuuint32_t box[4] = {32, 0, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  if (src == 1) {
+    if (d.in_mode != kRow) return false;
+    dims[0] = 2ull * d.n_in;
+    dims[1] = (cuuint64_t)d.n_group;
+    strides_el[0] = d.in_g;
+    box[1] = kTileP;
+  } else {
+    if (d.in_mode != kCol) return false;
+    dims[0] = 2ull * d.n_group;
+    dims[1] = (cuuint64_t)d.n_in;
+    strides_el[0] = d.in_n;
+    box[1] = 32;
+  }
+  dims[2] = (cuuint64_t)d.n_outer;
+  dims[3] = (cuuint64_t)d.batch;
+  strides_el[1] = d.in_o;
+  strides_el[2] = d.in_b;
+  cuuint64_t strides[3];
+  for (int i = 0; i < 3; ++i) {
+    long long bytes = strides_el[i] * 8;
+    if (dims[i + 1] == 1) bytes = std::max<long long>(16, (bytes + 15) / 16 * 16);  // unused coordinate
+    if (bytes <= 0 || bytes % 16 != 0 || bytes >= (1LL << 40)) return false;
+    strides[i] = (cuuint64_t)bytes;
+  }
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(d.in), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
 
 // Per-device launch facts of one kernel (max dynamic smem set, blocks per SM).
 struct LaunchInfo {
@@ -197,6 +280,7 @@ static StageDesc mk(const void* in, void* out, int L, int kind, int dir, int bat
   d.interior = interior;
   d.tw = tw;
   d.tw2 = tw2;
+  d.tw_len = tw_table_len(L);
   d.dep_rule = kDepNone;
   return d;
 }
@@ -416,8 +500,26 @@ static const PersistentKernel* find_persistent(const Pipeline& P) {
   return nullptr;
 }
 
-static int launch_stage(const StageDesc& d, cudaStream_t stream) {
+// Launch one stage: the TMA kernel when one exists for the stage and its input
+// layout can be described by a tensor map, else the load/store kernel.
+static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags = 0, int* err = nullptr) {
   if (d.n_tiles == 0) return GBFFT_OK;
+  if (!(flags & GBFFT_NO_TMA) && err && d.kind != kIdentity) {
+    const int src = d.in_mode == kRow ? 1 : 2;
+    const TmaKernel* tk = find_tma(d.L, d.dir, d.kind, src);
+    alignas(64) CUtensorMap map;
+    if (tk && encode_input_map(d, src, &map)) {
+      int bpsm = 1;
+      cudaError_t e = launch_info(tk->fn, tk->threads, tk->smem, &bpsm);
+      if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+      long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
+      StageDesc dd = d;
+      long long timeout_ns = 2000000000LL;
+      void* args[] = {&map, &dd, &err, &timeout_ns};
+      e = cudaLaunchKernel(tk->fn, dim3((unsigned)grid), dim3((unsigned)tk->threads), args, tk->smem, stream);
+      return cuda_err(e);
+    }
+  }
   const StageKernel* k = find_stage(d.L, d.dir, d.kind);
   if (!k) return GBFFT_ERR_UNSUPPORTED_SIZE;
   int bpsm = 1;
@@ -433,7 +535,9 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream) {
 namespace gbfft {
 // Launch one stage through the registry; used by the allocation-free entry
 // point in gbfft_static.cu.
-int launch_stage_external(const StageDesc& d, cudaStream_t stream) { return launch_stage(d, stream); }
+int launch_stage_external(const StageDesc& d, cudaStream_t stream) {
+  return launch_stage(d, stream, GBFFT_NO_TMA, nullptr);
+}
 }  // namespace gbfft
 
 static int ensure_workspace(gbfft_plan_s* p) {
@@ -478,7 +582,7 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
   const PersistentKernel* pk = staged ? nullptr : find_persistent(P);
   if (!pk) {
     for (int s = 0; s < P.n; ++s) {
-      int rc = launch_stage(P.st[s], stream);
+      int rc = launch_stage(P.st[s], stream, p->flags, &p->ctl->error);
       if (rc) return rc;
     }
     return GBFFT_OK;
@@ -537,11 +641,36 @@ static std::vector<float2> twiddle_table(int n, int count) {
   std::vector<float2> h((size_t)count);
   const double two_pi = 6.283185307179586476925286766559;
   for (int t = 0; t < count; ++t) {
-    double a = two_pi * (double)(t % n) / (double)n;
+    double a = two_pi * ((double)(t % n) / (double)n);
     h[(size_t)t] = make_float2((float)std::cos(a), (float)-std::sin(a));
   }
   return h;
 }
+
+namespace gbfft {
+// Packed Stockham twiddles of length L (the device layout of tw_table_len):
+// pass i >= 1 with prefix Ns and radix R stores W_{Ns R}^{r k} at k R + r.
+// Each value is exp(-2 pi i r k / (Ns R)) in FP64, rounded once to FP32.
+std::vector<float2> packed_twiddles(int L) {
+  int rad[16];
+  const int np = host_radices(L, rad, 16);
+  std::vector<float2> h;
+  const double two_pi = 6.283185307179586476925286766559;
+  long long ns = np > 0 ? rad[0] : 1;
+  for (int i = 1; i < np; ++i) {
+    const int R = rad[i];
+    const long long m = ns * R;
+    for (long long k = 0; k < ns; ++k)
+      for (int r = 0; r < R; ++r) {
+        double a = two_pi * ((double)((r * k) % m) / (double)m);
+        h.push_back(make_float2((float)std::cos(a), (float)-std::sin(a)));
+      }
+    ns = m;
+  }
+  if (h.empty()) h.push_back(make_float2(1.f, 0.f));
+  return h;
+}
+}  // namespace gbfft
 
 static void free_plan(gbfft_plan_s* p) {
   if (!p) return;
@@ -625,7 +754,7 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   if (nx < 2 || ny < 2 || nz < 2 || batch < 1) return GBFFT_ERR_INVALID_ARG;
   if (kind != GBFFT_C2C && kind != GBFFT_R2C) return GBFFT_ERR_INVALID_ARG;
   if (dtype != GBFFT_FP32) return GBFFT_ERR_INVALID_ARG;
-  const unsigned known = GBFFT_SLAB | GBFFT_TRANSPOSED_OUT | GBFFT_STAGED | GBFFT_DEBUG_TIMEOUT;
+  const unsigned known = GBFFT_SLAB | GBFFT_TRANSPOSED_OUT | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT;
   if (flags & ~known) return GBFFT_ERR_INVALID_ARG;
   if ((flags & GBFFT_SLAB) && (flags & GBFFT_TRANSPOSED_OUT)) return GBFFT_ERR_INVALID_ARG;
   if (kind == GBFFT_R2C && (nx % 2 != 0 || nx < 4)) return GBFFT_ERR_INVALID_ARG;
@@ -666,9 +795,9 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   else
     p->n_ws = kind == GBFFT_R2C ? 1 : 0;
 
-  p->tw_x = upload_table(twiddle_table(Lx, Lx));
-  p->tw_y = upload_table(twiddle_table(ny, ny));
-  p->tw_z = upload_table(twiddle_table(nz, nz));
+  p->tw_x = upload_table(packed_twiddles(Lx));
+  p->tw_y = upload_table(packed_twiddles(ny));
+  p->tw_z = upload_table(packed_twiddles(nz));
   bool ok = p->tw_x && p->tw_y && p->tw_z;
   if (ok && kind == GBFFT_R2C) {
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
@@ -844,7 +973,7 @@ int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* 
   d.interior = 1.f;
   d.dep_rule = kDepNone;
   if (identity) d.kind = kIdentity, d.dir = -1, d.n_in = d.n_out = d.L;
-  return launch_stage(d, reinterpret_cast<cudaStream_t>(stream));
+  return launch_stage(d, reinterpret_cast<cudaStream_t>(stream), plan->flags, &plan->ctl->error);
 }
 
 // ------------------------------------------------------------- plan cache

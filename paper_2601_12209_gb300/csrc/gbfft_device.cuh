@@ -60,6 +60,21 @@ __host__ __device__ constexpr int radix_prefix(int L, int pass) {
   return ns;
 }
 
+// Packed twiddle table of a length-L transform: pass i >= 1 (radix R_i,
+// prefix Ns_i) owns Ns_i * R_i entries, entry k * R_i + r holding
+// W_{Ns_i R_i}^{r k} = exp(-2 pi i r k / (Ns_i R_i)) (r = 0 holds 1). A
+// butterfly's R_i - 1 twiddles then sit next to each other (16-byte pairs).
+__host__ __device__ constexpr int tw_pass_offset(int L, int pass) {
+  int off = 0;
+  for (int i = 1; i < pass; ++i) off += radix_prefix(L, i) * make_radices(L).r[i];
+  return off;
+}
+__host__ __device__ constexpr int tw_table_len(int L) {
+  const int n = make_radices(L).n;
+  const int t = tw_pass_offset(L, n);
+  return t > 0 ? t : 1;
+}
+
 // Groups of 16 threads that share the butterflies of a pass: the largest
 // power of two not above the smallest butterfly count of any pass, capped at
 // 32 (512 threads).
@@ -258,7 +273,9 @@ __device__ __forceinline__ void dft(float2* a) {
 // The 16 pencils of one index n form one 128-byte row; the 16-byte chunk
 // (pencil pair) index is XOR-ed with n mod 8, so both "16 pencils at one n"
 // and "one pencil pair over 8 consecutive n" touch every bank once.
-__device__ __forceinline__ int swz(int n, int p) { return (n << 4) | ((((p >> 1) ^ (n & 7)) << 1) | (p & 1)); }
+// XOR-ing the 16-byte chunk index (p >> 1) with (n & 7) equals XOR-ing p with
+// 2 (n & 7), since the mask is even and leaves bit 0 of p alone.
+__device__ __forceinline__ int swz(int n, int p) { return (n << 4) + (p ^ ((n & 7) << 1)); }
 
 __device__ __forceinline__ float2 ld_data(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ void st_data(float2* p, float2 v) { __stcg(p, v); }
@@ -287,12 +304,15 @@ __device__ __forceinline__ void row_load(float2* sm, const TileIO& io) {
 
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
+  const float sc = io.scale;
+  const bool unit = sc == 1.f;
   for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float4 v = *reinterpret_cast<const float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1)));
-    if (p0 < io.valid) st_data(io.gout + p0 * io.out_g + n, make_float2(v.x * io.scale, v.y * io.scale));
-    if (p0 + 1 < io.valid) st_data(io.gout + (p0 + 1) * io.out_g + n, make_float2(v.z * io.scale, v.w * io.scale));
+    if (!unit) v = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
+    if (p0 < io.valid) st_data(io.gout + p0 * io.out_g + n, make_float2(v.x, v.y));
+    if (p0 + 1 < io.valid) st_data(io.gout + (p0 + 1) * io.out_g + n, make_float2(v.z, v.w));
   }
 }
 
@@ -327,13 +347,19 @@ __device__ __forceinline__ void col_store(const float2* sm, const TileIO& io) {
 // y[(j - k) R + k + q Ns]. Thread (p, g) owns butterflies j = g + t*G.
 //   SRC_GLOBAL: pass 0 reads the column-side input straight from HBM.
 //   DST_GLOBAL: the last pass writes the column-side output straight to HBM.
-template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, bool SYNC_BEFORE_WRITE>
+// Row-side box layout written by the tensor copies (see gbfft_tma.cuh):
+// index n of pencil p, 16-index boxes of 16 pencil rows, 128-byte swizzle.
+__device__ __forceinline__ int rowbox_index(int n, int p) {
+  return ((n >> 4) << 8) | (p << 4) | ((((n & 15) >> 1) ^ (p & 7)) << 1) | (n & 1);
+}
+
+template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, bool SYNC_BEFORE_WRITE,
+          int SRC_LAYOUT = 0>
 __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, const TileIO& io) {
   constexpr Radices RP = make_radices(L);
   constexpr int R = RP.r[PASS];
   constexpr int Ns = radix_prefix(L, PASS);
   constexpr int NB = L / R;
-  constexpr int S = L / (Ns * R);
   constexpr int G = THREADS / 16;
   constexpr int NBT = (NB + G - 1) / G;
   const int p = threadIdx.x & 15, g = threadIdx.x >> 4;
@@ -347,28 +373,45 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
         const int n = j + r * NB;
         if constexpr (SRC_GLOBAL) {
           v[t][r] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
+        } else if constexpr (SRC_LAYOUT == 1) {
+          v[t][r] = sm[rowbox_index(n, p)];
         } else {
           v[t][r] = sm[swz(n, p)];
         }
       }
       if constexpr (Ns > 1) {
         const int k = j % Ns;
+        const float2* twp = tw + tw_pass_offset(L, PASS) + k * R;
+        if constexpr (R % 2 == 0) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[t][r] = cmul(v[t][r], tw_dir<DIR>(tw[r * k * S]));
+          for (int r = 0; r < R; r += 2) {
+            const float4 w = *reinterpret_cast<const float4*>(twp + r);
+            if (r > 0) v[t][r] = cmul(v[t][r], tw_dir<DIR>(make_float2(w.x, w.y)));
+            v[t][r + 1] = cmul(v[t][r + 1], tw_dir<DIR>(make_float2(w.z, w.w)));
+          }
+        } else {
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[t][r] = cmul(v[t][r], tw_dir<DIR>(twp[r]));
+        }
       }
       dft<R, DIR>(v[t]);
     }
   }
   if constexpr (DST_GLOBAL) {
     if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
+    const bool unit = io.scale == 1.f;
 #pragma unroll
     for (int t = 0; t < NBT; ++t) {
       const int j = g + t * G;
       if ((NB % G == 0 || j < NB) && p < io.valid) {
+        float2* o = io.gout + p + (long long)j * io.out_n;
+        const long long step = (long long)NB * io.out_n;  // last pass: Ns R = L, outputs j + q NB
+        if (unit) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const int n = j + q * NB;  // last pass: Ns R = L
-          st_data(io.gout + p + n * io.out_n, make_float2(v[t][q].x * io.scale, v[t][q].y * io.scale));
+          for (int q = 0; q < R; ++q) st_data(o + q * step, v[t][q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < R; ++q) st_data(o + q * step, cscale(v[t][q], io.scale));
         }
       }
     }
@@ -389,7 +432,10 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
 
 // All passes of a length-L transform. The data starts in shared memory unless
 // SRC_GLOBAL, and ends in shared memory unless DST_GLOBAL.
-template <int L, int DIR, int THREADS, bool SRC_GLOBAL, bool DST_GLOBAL, bool INPLACE_GLOBAL, int PASS = 0>
+// SRC_LAYOUT selects how pass 0 reads shared memory: 0 the swizzled column
+// layout swz(), 1 the row-side box layout of the tensor copies.
+template <int L, int DIR, int THREADS, bool SRC_GLOBAL, bool DST_GLOBAL, bool INPLACE_GLOBAL, int PASS = 0,
+          int SRC_LAYOUT = 0>
 __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const TileIO& io) {
   constexpr int NP = make_radices(L).n;
   if constexpr (PASS < NP) {
@@ -398,8 +444,8 @@ __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const T
     // before overwriting shared memory, everyone must have read it; a direct
     // global->global single pass in place also needs the barrier
     constexpr bool sync_w = (!src_g && !dst_g) || (src_g && dst_g && INPLACE_GLOBAL);
-    stockham_pass<L, DIR, THREADS, PASS, src_g, dst_g, sync_w>(sm, tw, io);
-    fft_passes<L, DIR, THREADS, SRC_GLOBAL, DST_GLOBAL, INPLACE_GLOBAL, PASS + 1>(sm, tw, io);
+    stockham_pass<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, PASS == 0 ? SRC_LAYOUT : 0>(sm, tw, io);
+    fft_passes<L, DIR, THREADS, SRC_GLOBAL, DST_GLOBAL, INPLACE_GLOBAL, PASS + 1, SRC_LAYOUT>(sm, tw, io);
   }
 }
 
@@ -587,7 +633,7 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
 // Copy a stage's twiddle tables into shared memory.
 template <int L, int THREADS>
 __device__ __forceinline__ void load_twiddles(float2* tw_s, float2* tw2_s, const StageDesc& d, bool need_tw2) {
-  for (int i = threadIdx.x; i < L; i += THREADS) tw_s[i] = d.tw[i];
+  for (int i = threadIdx.x; i < tw_table_len(L); i += THREADS) tw_s[i] = d.tw[i];
   if (need_tw2)
     for (int i = threadIdx.x; i <= L; i += THREADS) tw2_s[i] = d.tw2[i];
 }

@@ -58,8 +58,9 @@ struct StageDesc {
   int dir;       // -1 forward sign, +1 inverse sign
   float scale;     // multiplies every output value
   float interior;  // R2C/C2R: multiplies bins 1..L-1 of the half spectrum
-  const float2* tw;    // W_L^t = exp(-2 pi i t / L), t in [0, L)   (device)
+  const float2* tw;    // packed per-pass twiddles of length L (tw_table_len(L) entries, device)
   const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R only)
+  int tw_len;          // entries of tw
   // Poisson z stage: wavenumber bookkeeping of the tile's pencils
   int pz_nx, pz_ny;    // full grid nx, ny (kx of pencil = group index, ky = outer index)
   // persistent-kernel dependency rule on the previous stage

@@ -26,16 +26,25 @@ struct PersistentKernel {
   size_t tw_smem_per_stage;  // twiddle bytes per stage (total = smem + nstages * this)
 };
 
+// A TMA stage kernel (gbfft_tma.cuh): input tiles arrive by tensor copies.
+struct TmaKernel {
+  int L, dir, kind, src;  // src: 1 row-side copies, 2 column-side copies
+  const void* fn;
+  int threads;
+  size_t smem;
+};
+
 constexpr int kcode(int L, int kind, int dir) { return (L << 8) | (kind << 1) | (dir > 0 ? 1 : 0); }
 
 std::vector<StageKernel>& stage_registry();
 std::vector<PersistentKernel>& persistent_registry();
+std::vector<TmaKernel>& tma_registry();
 
 // --------------------------------------------------------- stage kernel
 
 template <int L, int KIND>
 constexpr size_t stage_smem_bytes() {
-  return sizeof(float2) * ((size_t)(L + 1) * kTileP + L + (L + 1));
+  return sizeof(float2) * ((size_t)(L + 1) * kTileP + tw_table_len(L) + (L + 1));
 }
 
 // One launch per stage. Each block loops over tiles with a grid stride, so
@@ -46,7 +55,7 @@ __global__ void __launch_bounds__(threads_for(L), min_blocks_for(L)) stage_kerne
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* tw = sm + (L + 1) * kTileP;
-  float2* tw2 = tw + L;
+  float2* tw2 = tw + tw_table_len(L);
   load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre);
   __syncthreads();
   for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
@@ -212,9 +221,20 @@ template <int... CODES>
 constexpr size_t persistent_tile_bytes() {
   return sizeof(float2) * (size_t)(max_len<CODES...>() + 1) * kTileP;
 }
+template <int CODE, int... REST>
+__host__ __device__ constexpr int max_tw_len() {
+  if constexpr (sizeof...(REST) == 0) return tw_table_len(CODE >> 8);
+  else return tw_table_len(CODE >> 8) > max_tw_len<REST...>() ? tw_table_len(CODE >> 8) : max_tw_len<REST...>();
+}
+
+// per stage: the packed twiddles, then W_2L (real transforms)
+template <int... CODES>
+__host__ __device__ constexpr int persistent_tw_block() {
+  return max_tw_len<CODES...>() + max_len<CODES...>() + 1;
+}
 template <int... CODES>
 constexpr size_t persistent_tw_bytes_per_stage() {
-  return sizeof(float2) * (size_t)(2 * max_len<CODES...>() + 1);
+  return sizeof(float2) * (size_t)persistent_tw_block<CODES...>();
 }
 
 __device__ __forceinline__ int stage_code(const StageDesc& d) {
@@ -247,12 +267,14 @@ persistent_kernel(PersistentArgs a) {
     s_ticket = atomicAdd(&a.ctl->ticket, 1u);
   }
   __syncthreads();
+  constexpr int TWB = persistent_tw_block<CODES...>();
+  constexpr int TW2 = max_tw_len<CODES...>();
   for (int s = 0; s < a.nstages; ++s) {
-    float2* tw = tws + s * (2 * LM + 1);
+    float2* tw = tws + s * TWB;
     const StageDesc& d = s_st[s];
-    for (int i = threadIdx.x; i < d.L; i += THREADS) tw[i] = d.tw[i];
+    for (int i = threadIdx.x; i < d.tw_len; i += THREADS) tw[i] = d.tw[i];
     if (d.kind == kR2CPost || d.kind == kC2RPre)
-      for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[LM + i] = d.tw2[i];
+      for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[TW2 + i] = d.tw2[i];
   }
   __syncthreads();
   unsigned int next = 0;
@@ -275,8 +297,8 @@ persistent_kernel(PersistentArgs a) {
     __syncthreads();
     if (!s_ok) break;
     const StageDesc& d = s_st[s];
-    const float2* tw = tws + s * (2 * LM + 1);
-    dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile, sm, tw, tw + LM);
+    const float2* tw = tws + s * TWB;
+    dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile, sm, tw, tw + TW2);
     __syncthreads();
     if (threadIdx.x == 0) {
       signal_done(a, s_st, s, tile);

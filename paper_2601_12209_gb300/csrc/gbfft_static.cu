@@ -25,6 +25,7 @@
 
 namespace gbfft {
 int launch_stage_external(const StageDesc& d, cudaStream_t stream);
+std::vector<float2> packed_twiddles(int L);
 }
 
 using namespace gbfft;
@@ -35,9 +36,9 @@ namespace {
 // grid point, GBFFT_NOALLOC_MAX_POINTS points (32 MiB). Shared by every call.
 __device__ __align__(256) float2 g_noalloc_scratch[GBFFT_NOALLOC_MAX_POINTS];
 
-// Twiddle tables W_L^t = exp(-2 pi i t/L), t in [0, L), for every supported
-// length L, packed one after another.
-constexpr int kTwCapacity = 8192;
+// Packed twiddle tables (the stage kernels' layout) for every supported
+// length L, one after another.
+constexpr int kTwCapacity = 16384;
 __device__ __align__(256) float2 g_noalloc_twiddles[kTwCapacity];
 
 constexpr int kMaxLen = 1024;
@@ -70,16 +71,13 @@ int setup_device(int dev, DeviceState** out) {
   st.tw = reinterpret_cast<float2*>(p);
   std::vector<float2> host;
   host.reserve(kTwCapacity);
-  const double two_pi = 6.283185307179586476925286766559;
   for (int L = 0; L <= kMaxLen; ++L) {
     st.tw_offset[L] = -1;
     if (L < 2 || !gbfft_supported_length(L)) continue;
-    if ((int)host.size() + L > kTwCapacity) return GBFFT_ERR_CUDA;
+    const std::vector<float2> t = packed_twiddles(L);
+    if ((int)(host.size() + t.size()) > kTwCapacity) return GBFFT_ERR_CUDA;
     st.tw_offset[L] = (int)host.size();
-    for (int t = 0; t < L; ++t) {
-      double a = two_pi * (double)t / (double)L;
-      host.push_back(make_float2((float)std::cos(a), (float)-std::sin(a)));
-    }
+    host.insert(host.end(), t.begin(), t.end());
   }
   if (cudaMemcpyToSymbol(g_noalloc_twiddles, host.data(), host.size() * sizeof(float2)) != cudaSuccess)
     return GBFFT_ERR_CUDA;
@@ -118,6 +116,7 @@ StageDesc stage(const void* in, void* out, int L, int dir, int n_outer, int n_gr
   d.scale = scale;
   d.interior = 1.f;
   d.tw = tw;
+  d.tw_len = tw_table_len(L);
   return d;
 }
 

@@ -30,12 +30,13 @@ def err(name, got, ref):
     return e
 
 
-@pytest.mark.parametrize("slab", [False, True], ids=["pencil", "slab"])
-def test_r2c_c2r_512(gb, slab):
+@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+def test_r2c_c2r_512(gb, mode):
     """Config: R2C forward and C2R inverse at 512^3 FP32, real N(0,1) input."""
     n = 512
+    slab = mode == "slab"
     r = synth.normal_real((n, n, n), seed=2)
-    plan = gb.Plan(n, n, n, kind="r2c", slab=slab)
+    plan = gb.Plan(n, n, n, kind="r2c", slab=slab, staged=(mode == "pencil_staged"))
     rd = r.cuda()
     H = plan.forward(rd)
     r2 = plan.inverse(H)
@@ -43,7 +44,7 @@ def test_r2c_c2r_512(gb, slab):
     assert plan.device_error() == 0
     Hh = H.cpu().numpy()
     ref = oracle.rfft3(r.numpy())
-    assert err(f"r2c 512 fwd {'slab' if slab else 'pencil'}", Hh, ref) < TOL
+    assert err(f"r2c 512 fwd {mode}", Hh, ref) < TOL
     # direct triple-sum DFT at sampled bins (no factorisation involved)
     rng = np.random.default_rng(5)
     bins = [(int(rng.integers(0, n // 2 + 1)), int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(4)]
@@ -51,23 +52,24 @@ def test_r2c_c2r_512(gb, slab):
     got = np.array([Hh[kz, ky, kx] for (kx, ky, kz) in bins])
     assert err("r2c 512 direct-DFT samples", got, direct) < TOL
     del ref, Hh
-    assert err(f"r2c 512 roundtrip {'slab' if slab else 'pencil'}", r2.cpu().numpy(), r.numpy()) < TOL
+    assert err(f"r2c 512 roundtrip {mode}", r2.cpu().numpy(), r.numpy()) < TOL
 
 
-@pytest.mark.parametrize("slab", [False, True], ids=["pencil", "slab"])
-def test_c2c_512(gb, slab):
+@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+def test_c2c_512(gb, mode):
     """Spec target: C2C forward+inverse at 512^3, complex64 uniform[-1,1]."""
     n = 512
+    slab = mode == "slab"
     x = synth.uniform_complex((n, n, n), seed=3)
-    plan = gb.Plan(n, n, n, slab=slab)
+    plan = gb.Plan(n, n, n, slab=slab, staged=(mode == "pencil_staged"))
     X = plan.forward(x.cuda())
     torch.cuda.synchronize()
     Xh = X.cpu().numpy()
     ref = oracle.fft3(x.numpy())
-    assert err(f"c2c 512 fwd {'slab' if slab else 'pencil'}", Xh, ref) < TOL
+    assert err(f"c2c 512 fwd {mode}", Xh, ref) < TOL
     del ref
     xr = plan.inverse(X)
-    assert err(f"c2c 512 roundtrip {'slab' if slab else 'pencil'}", xr.cpu().numpy(), x.numpy()) < TOL
+    assert err(f"c2c 512 roundtrip {mode}", xr.cpu().numpy(), x.numpy()) < TOL
     assert plan.device_error() == 0
 
 

@@ -42,12 +42,22 @@ C2C_SHAPES = [  # (nx, ny, nz, batch)
 ]
 
 
+MODES = ["pencil", "pencil_staged", "pencil_staged_lsu", "slab", "slab_staged"]
+
+
+def make_plan(gb, nx, ny, nz, mode, **kw):
+    """pencil: persistent launch; *_staged: one launch per stage (tensor-copy loads where the
+    layout allows); *_lsu: staged with thread loads only."""
+    return gb.Plan(nx, ny, nz, slab=mode.startswith("slab"), staged="staged" in mode, tma=not mode.endswith("lsu"),
+                   **kw)
+
+
 @pytest.mark.parametrize("shape", C2C_SHAPES, ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+@pytest.mark.parametrize("mode", MODES)
 def test_c2c_forward_inverse(gb, shape, mode):
     nx, ny, nz, b = shape
     x = synth.uniform_complex((b, nz, ny, nx), seed=1 + nx + ny + nz)
-    plan = gb.Plan(nx, ny, nz, batch=b, slab=(mode == "slab"), staged=(mode == "pencil_staged"))
+    plan = make_plan(gb, nx, ny, nz, mode, batch=b)
     xd = x.to(dev())
     X = plan.forward(xd)
     xr = plan.inverse(X)
@@ -89,11 +99,11 @@ R2C_SHAPES = [(8, 8, 8, 1), (64, 64, 64, 1), (16, 12, 10, 2), (60, 48, 80, 1), (
 
 
 @pytest.mark.parametrize("shape", R2C_SHAPES, ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+@pytest.mark.parametrize("mode", MODES)
 def test_r2c_c2r(gb, shape, mode):
     nx, ny, nz, b = shape
     r = synth.normal_real((b, nz, ny, nx), seed=2 + nx)
-    plan = gb.Plan(nx, ny, nz, kind="r2c", batch=b, slab=(mode == "slab"), staged=(mode == "pencil_staged"))
+    plan = make_plan(gb, nx, ny, nz, mode, kind="r2c", batch=b)
     H = plan.forward(r.to(dev()))
     r2 = plan.inverse(H)
     torch.cuda.synchronize()
@@ -219,16 +229,21 @@ def test_each_stage_alone(gb, shape):
 
 
 def test_persistent_equals_staged_bitwise(gb):
-    """The persistent launch runs the same tile arithmetic as the per-stage launches."""
-    for kind, shape in (("c2c", (64, 64, 64)), ("r2c", (64, 64, 64))):
+    """The persistent launch, the staged launches with tensor-copy loads and the staged
+    launches with thread loads run the same tile arithmetic: identical bits."""
+    for kind, shape in (("c2c", (64, 64, 64)), ("r2c", (64, 64, 64)), ("c2c", (512, 64, 32)),
+                        ("r2c", (512, 32, 64))):
         nx, ny, nz = shape
         x = synth.uniform_complex((nz, ny, nx), seed=21) if kind == "c2c" else synth.normal_real((nz, ny, nx), 22)
         p1 = gb.Plan(nx, ny, nz, kind=kind)
         p2 = gb.Plan(nx, ny, nz, kind=kind, staged=True)
+        p3 = gb.Plan(nx, ny, nz, kind=kind, staged=True, tma=False)
         a = p1.forward(x.to(dev()))
         b = p2.forward(x.to(dev()))
-        assert torch.equal(a, b)
-        assert torch.equal(p1.inverse(a), p2.inverse(b))
+        c = p3.forward(x.to(dev()))
+        assert torch.equal(a, b) and torch.equal(a, c)
+        assert torch.equal(p1.inverse(a), p2.inverse(b)) and torch.equal(p1.inverse(a), p3.inverse(c))
+        assert p1.device_error() == 0 and p2.device_error() == 0 and p3.device_error() == 0
 
 
 def test_device_timeout_is_reported_not_hung(gb):
