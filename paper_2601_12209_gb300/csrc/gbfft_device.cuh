@@ -381,6 +381,7 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
       }
       if constexpr (Ns > 1) {
         const int k = j % Ns;
+        // tw is 16-byte aligned and every offset below is even when R is even
         const float2* twp = tw + tw_pass_offset(L, PASS) + k * R;
         if constexpr (R % 2 == 0) {
 #pragma unroll

@@ -227,10 +227,12 @@ __host__ __device__ constexpr int max_tw_len() {
   else return tw_table_len(CODE >> 8) > max_tw_len<REST...>() ? tw_table_len(CODE >> 8) : max_tw_len<REST...>();
 }
 
-// per stage: the packed twiddles, then W_2L (real transforms)
+// per stage: the packed twiddles, then W_2L (real transforms); a multiple of
+// 8 entries so every stage's table starts 64-byte aligned (the butterflies
+// read twiddle pairs as 16-byte loads)
 template <int... CODES>
 __host__ __device__ constexpr int persistent_tw_block() {
-  return max_tw_len<CODES...>() + max_len<CODES...>() + 1;
+  return (max_tw_len<CODES...>() + max_len<CODES...>() + 1 + 7) / 8 * 8;
 }
 template <int... CODES>
 constexpr size_t persistent_tw_bytes_per_stage() {
