@@ -141,6 +141,39 @@ int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream)
  */
 int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out);
 
+/*
+ * Autotuner (Section V-B: plans pick the best execution strategy for a size
+ * and transform type; Section III-C: the granularity/overhead trade-off).
+ * For each pipeline of the plan -- 0 forward (FORWARD, INVERSE_ADJOINT),
+ * 1 inverse (INVERSE, ADJOINT), 2 Poisson (R2C plans) -- it times on
+ * `stream`, with CUDA events, every stage with the thread-load kernel and
+ * with the tensor-copy kernel (where one applies), and the whole pipeline as
+ * one persistent launch (where a kernel family exists); it keeps the fastest
+ * per-stage choice or the persistent launch, whichever is faster. Later exec
+ * calls use the choice. Blocking (synchronises `stream`); allocates the
+ * plan's workspace and two scratch buffers on first use; respects
+ * GBFFT_STAGED and GBFFT_NO_TMA. Do not call it during stream capture.
+ */
+int gbfft_plan_autotune(gbfft_plan plan, void* stream);
+/*
+ * The tuned choice of a pipeline (0, 1, 2 as above): *tuned 0/1,
+ * *persistent 0/1, *tma_mask bit s = stage s uses the tensor-copy kernel,
+ * *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
+ * staged candidates. Any output pointer may be NULL.
+ */
+int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask, float* ms,
+                          float* stage_ms);
+/*
+ * Per-launch timing inside exec calls: while enabled, each exec records a
+ * CUDA event on its stream before its first launch and after every launch.
+ * gbfft_plan_stage_times synchronises on the recorded events of `pipeline`,
+ * returns the average duration of each launch segment over the calls
+ * (avg_ms[0..4]; one segment for a persistent launch, one per stage for
+ * staged launches), the segment count and the call count, and releases them.
+ */
+int gbfft_plan_time_stages(gbfft_plan plan, int enable);
+int gbfft_plan_stage_times(gbfft_plan plan, int pipeline, float* avg_ms, int* nsegments, int* ncalls);
+
 /* Bytes of device workspace the plan needs (pencil: one or two spectrum-sized buffers). */
 int gbfft_workspace_size(gbfft_plan plan, size_t* bytes);
 /* Give the plan caller-owned workspace (>= gbfft_workspace_size bytes, 256-byte aligned). */

@@ -143,6 +143,12 @@ class Plan:
         abi.gbfft_debug_run(self.handle, int(step), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
+    def autotune(self, stream=None) -> dict:
+        """Time the kernel variants per stage and the persistent launch; keep the fastest."""
+        abi.gbfft_plan_autotune(self.handle, _stream_handle(stream))
+        return {name: abi.gbfft_plan_get_tuning(self.handle, k)
+                for k, name in enumerate(("forward", "inverse", "poisson")) if k < 2 or self.kind == "r2c"}
+
     def workspace_size(self) -> int:
         return abi.gbfft_workspace_size(self.handle)
 

@@ -47,6 +47,7 @@ EXPORTED = (
     "gbfft_exec_poisson", "gbfft_exec_host", "gbfft_workspace_size", "gbfft_set_workspace",
     "gbfft_get_device_error", "gbfft_debug_run", "gbfft_strerror", "gbfft_plan_destroy",
     "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version", "gbfft_exec_c2c_noalloc",
+    "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
 )
 
 _lib = None
@@ -92,6 +93,12 @@ def load() -> ctypes.CDLL:
             "gbfft_radix_plan": (i, [i, ctypes.POINTER(i), i]),
             "gbfft_version": (ctypes.c_char_p, []),
             "gbfft_exec_c2c_noalloc": (i, [i, i, i, i, vp, vp, vp]),
+            "gbfft_plan_autotune": (i, [vp, vp]),
+            "gbfft_plan_get_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(u),
+                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+            "gbfft_plan_time_stages": (i, [vp, i]),
+            "gbfft_plan_stage_times": (i, [vp, i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i),
+                                           ctypes.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -209,6 +216,33 @@ def gbfft_exec_c2c_noalloc(nx: int, ny: int, nz: int, op: int, in_ptr: int, out_
     """Allocation-free C2C transform on one grid; see include/gbfft.h."""
     _call("gbfft_exec_c2c_noalloc", int(nx), int(ny), int(nz), int(op), ctypes.c_void_p(in_ptr),
           ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
+
+
+def gbfft_plan_autotune(plan: int, stream: int = 0) -> None:
+    _call("gbfft_plan_autotune", ctypes.c_void_p(plan), ctypes.c_void_p(stream))
+
+
+def gbfft_plan_get_tuning(plan: int, pipeline: int) -> dict:
+    tuned, pers = ctypes.c_int(), ctypes.c_int()
+    mask = ctypes.c_uint()
+    ms = ctypes.c_float()
+    stage = (ctypes.c_float * 5)()
+    _call("gbfft_plan_get_tuning", ctypes.c_void_p(plan), int(pipeline), ctypes.byref(tuned), ctypes.byref(pers),
+          ctypes.byref(mask), ctypes.byref(ms), stage)
+    return {"tuned": bool(tuned.value), "persistent": bool(pers.value), "tma_mask": mask.value, "ms": ms.value,
+            "stage_ms": [stage[k] for k in range(5)]}
+
+
+def gbfft_plan_time_stages(plan: int, enable: bool) -> None:
+    _call("gbfft_plan_time_stages", ctypes.c_void_p(plan), int(bool(enable)))
+
+
+def gbfft_plan_stage_times(plan: int, pipeline: int) -> tuple[list[float], int]:
+    avg = (ctypes.c_float * 5)()
+    nseg, ncalls = ctypes.c_int(), ctypes.c_int()
+    _call("gbfft_plan_stage_times", ctypes.c_void_p(plan), int(pipeline), avg, ctypes.byref(nseg),
+          ctypes.byref(ncalls))
+    return [avg[k] for k in range(nseg.value)], ncalls.value
 
 
 def raw_rc(name: str, *args) -> int:

@@ -239,6 +239,21 @@ struct gbfft_plan_s {
   void* h_out_dev = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
   cudaStream_t h_stream = nullptr;
+  // autotuned launch choice per pipeline (forward, inverse, Poisson)
+  struct Tuning {
+    bool tuned = false;
+    bool persistent = false;
+    unsigned tma_mask = 0;  // bit s: stage s uses the tensor-copy kernel
+    float ms = 0.f;         // measured time of the chosen launch(es)
+    float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  } tune[3];
+  // optional per-stage event timing inside exec calls
+  bool time_stages = false;
+  struct TimedCall {
+    int pipe, nev;
+    cudaEvent_t ev[kMaxStages + 1];
+  };
+  std::vector<TimedCall> timed;
 };
 
 static int cuda_err(cudaError_t e) { return e == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA; }
@@ -575,18 +590,61 @@ static int validate(const Pipeline& P) {
   return GBFFT_OK;
 }
 
+// Events around a pipeline's launches when per-stage timing is on (one event
+// before the first launch and one after each launch, on the launching stream).
+static void record_event(gbfft_plan_s* p, cudaStream_t stream, int pipe, bool first) {
+  if (!p->time_stages) return;
+  if (first) {
+    gbfft_plan_s::TimedCall c;
+    c.pipe = pipe;
+    c.nev = 0;
+    p->timed.push_back(c);
+  }
+  gbfft_plan_s::TimedCall& c = p->timed.back();
+  if (c.nev > kMaxStages) return;
+  if (cudaEventCreate(&c.ev[c.nev]) != cudaSuccess) return;
+  cudaEventRecord(c.ev[c.nev], stream);
+  ++c.nev;
+}
+
+static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream);
+
+// Staged launches with an explicit per-stage kernel choice (bit s of tma_mask:
+// tensor-copy kernel for stage s when it can run there).
+static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe) {
+  record_event(p, stream, pipe, true);
+  for (int s = 0; s < P.n; ++s) {
+    const unsigned f = ((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA;
+    int rc = launch_stage(P.st[s], stream, f, &p->ctl->error);
+    if (rc) return rc;
+    record_event(p, stream, pipe, false);
+  }
+  return GBFFT_OK;
+}
+
 static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream_t stream) {
   int vrc = validate(P);
   if (vrc) return vrc;
+  if (p->tune[pipe].tuned) {
+    const PersistentKernel* pk = p->tune[pipe].persistent ? find_persistent(P) : nullptr;
+    if (pk) {
+      record_event(p, stream, pipe, true);
+      int rc = run_persistent(p, P, pk, stream);
+      record_event(p, stream, pipe, false);
+      return rc;
+    }
+    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe);
+  }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
   const PersistentKernel* pk = staged ? nullptr : find_persistent(P);
-  if (!pk) {
-    for (int s = 0; s < P.n; ++s) {
-      int rc = launch_stage(P.st[s], stream, p->flags, &p->ctl->error);
-      if (rc) return rc;
-    }
-    return GBFFT_OK;
-  }
+  if (!pk) return run_staged(p, P, (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu, stream, pipe);
+  record_event(p, stream, pipe, true);
+  int rc = run_persistent(p, P, pk, stream);
+  record_event(p, stream, pipe, false);
+  return rc;
+}
+
+static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream) {
   PersistentArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nstages = P.n;
@@ -613,7 +671,8 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
   const bool dbg = (p->flags & GBFFT_DEBUG_TIMEOUT) != 0;
   a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
   a.debug_never = dbg ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(p->ctl, 0, sizeof(Control) + p->counters_words * sizeof(unsigned int), stream);
+  cudaError_t e = cudaMemsetAsync(&p->ctl->ticket, 0, 2 * sizeof(unsigned int) + p->counters_words * sizeof(unsigned int),
+                                  stream);
   if (e != cudaSuccess) return GBFFT_ERR_CUDA;
   const size_t smem = pk->smem + (size_t)P.n * pk->tw_smem_per_stage;
   int bpsm = 1;
@@ -683,6 +742,8 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->h_in_dev);
   cudaFree(p->h_out_dev);
   if (p->h_stream) cudaStreamDestroy(p->h_stream);
+  for (auto& c : p->timed)
+    for (int k = 0; k < c.nev; ++k) cudaEventDestroy(c.ev[k]);
   delete p;
 }
 
@@ -974,6 +1035,152 @@ int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* 
   d.dep_rule = kDepNone;
   if (identity) d.kind = kIdentity, d.dir = -1, d.n_in = d.n_out = d.L;
   return launch_stage(d, reinterpret_cast<cudaStream_t>(stream), plan->flags, &plan->ctl->error);
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- autotuning
+
+// Whether stage d can run with the tensor-copy kernel (one exists for its
+// length/kind/side and its input layout has a tensor map).
+static bool tma_possible(const StageDesc& d) {
+  if (d.kind == kIdentity) return false;
+  const int src = d.in_mode == kRow ? 1 : 2;
+  if (!find_tma(d.L, d.dir, d.kind, src)) return false;
+  alignas(64) CUtensorMap m;
+  return encode_input_map(d, src, &m);
+}
+
+// Average time of `reps` back-to-back calls of f on `stream` after one warm-up
+// call (CUDA events on the launching stream). Negative on failure.
+template <typename F>
+static float time_calls(F f, cudaStream_t stream, int reps) {
+  if (f() != GBFFT_OK) return -1.f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  cudaEventRecord(e0, stream);
+  bool ok = true;
+  for (int i = 0; i < reps && ok; ++i) ok = f() == GBFFT_OK;
+  cudaEventRecord(e1, stream);
+  float ms = -1.f;
+  if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+    ms /= (float)reps;
+  else
+    ms = -1.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+extern "C" {
+
+int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
+  if (!plan) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  int rc = ensure_workspace(plan);
+  if (rc) return rc;
+  const size_t big = std::max(op_in_bytes(plan, 0), op_out_bytes(plan, 0));
+  if (!plan->h_in_dev) {
+    if (cudaMalloc(&plan->h_in_dev, big) != cudaSuccess || cudaMalloc(&plan->h_out_dev, big) != cudaSuccess) {
+      cudaGetLastError();
+      return GBFFT_ERR_ALLOC;
+    }
+    plan->h_in_bytes = plan->h_out_bytes = big;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(plan->h_in_dev, 0, big, st) != cudaSuccess) return GBFFT_ERR_CUDA;
+  const bool was_timing = plan->time_stages;
+  plan->time_stages = false;
+  const int npipes = plan->kind == GBFFT_R2C ? 3 : 2;
+  const int reps = 5;
+  for (int pipe = 0; pipe < npipes; ++pipe) {
+    const int op = pipe == kPipeFwd ? GBFFT_OP_FORWARD : (pipe == kPipeInv ? GBFFT_OP_INVERSE : 4);
+    Buf bin{plan->h_in_dev, (long long)(big / sizeof(float2))};
+    Buf bout{plan->h_out_dev, (long long)(big / sizeof(float2))};
+    Pipeline P = build_pipeline(plan, pipe, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
+    rc = validate(P);
+    if (rc) return rc;
+    gbfft_plan_s::Tuning t;
+    float staged_ms = 0.f;
+    for (int s = 0; s < P.n; ++s) {
+      const StageDesc d = P.st[s];
+      float best = time_calls([&] { return launch_stage(d, st, GBFFT_NO_TMA, &plan->ctl->error); }, st, reps);
+      if (best < 0.f) return GBFFT_ERR_CUDA;
+      if (!(plan->flags & GBFFT_NO_TMA) && tma_possible(d)) {
+        float tt = time_calls([&] { return launch_stage(d, st, 0u, &plan->ctl->error); }, st, reps);
+        if (tt >= 0.f && tt < best) {
+          best = tt;
+          t.tma_mask |= 1u << s;
+        }
+      }
+      t.stage_ms[s] = best;
+      staged_ms += best;
+    }
+    t.ms = staged_ms;
+    const PersistentKernel* pk = (plan->flags & GBFFT_STAGED) ? nullptr : find_persistent(P);
+    if (pk) {
+      float tp = time_calls([&] { return run_persistent(plan, P, pk, st); }, st, reps);
+      if (tp >= 0.f && tp < staged_ms) {
+        t.persistent = true;
+        t.ms = tp;
+      }
+    }
+    t.tuned = true;
+    plan->tune[pipe] = t;
+  }
+  plan->time_stages = was_timing;
+  return cuda_err(cudaStreamSynchronize(st));
+}
+
+int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask,
+                          float* ms, float* stage_ms) {
+  if (!plan || pipeline < 0 || pipeline > 2) return GBFFT_ERR_INVALID_ARG;
+  const gbfft_plan_s::Tuning& t = plan->tune[pipeline];
+  if (tuned) *tuned = t.tuned ? 1 : 0;
+  if (persistent) *persistent = t.persistent ? 1 : 0;
+  if (tma_mask) *tma_mask = t.tma_mask;
+  if (ms) *ms = t.ms;
+  if (stage_ms)
+    for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
+  return GBFFT_OK;
+}
+
+int gbfft_plan_time_stages(gbfft_plan plan, int enable) {
+  if (!plan) return GBFFT_ERR_INVALID_ARG;
+  plan->time_stages = enable != 0;
+  return GBFFT_OK;
+}
+
+int gbfft_plan_stage_times(gbfft_plan plan, int pipeline, float* avg_ms, int* nsegments, int* ncalls) {
+  if (!plan || !avg_ms || !nsegments || !ncalls || pipeline < 0 || pipeline > 2) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  for (int s = 0; s < kMaxStages; ++s) avg_ms[s] = 0.f;
+  *nsegments = 0;
+  *ncalls = 0;
+  std::vector<gbfft_plan_s::TimedCall> keep;
+  for (auto& c : plan->timed) {
+    if (c.pipe != pipeline) {
+      keep.push_back(c);
+      continue;
+    }
+    if (c.nev >= 2 && cudaEventSynchronize(c.ev[c.nev - 1]) == cudaSuccess) {
+      for (int s = 0; s + 1 < c.nev; ++s) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c.ev[s], c.ev[s + 1]) == cudaSuccess) avg_ms[s] += ms;
+      }
+      *nsegments = std::max(*nsegments, c.nev - 1);
+      ++*ncalls;
+    }
+    for (int k = 0; k < c.nev; ++k) cudaEventDestroy(c.ev[k]);
+  }
+  plan->timed.swap(keep);
+  if (*ncalls > 0)
+    for (int s = 0; s < kMaxStages; ++s) avg_ms[s] /= (float)*ncalls;
+  return GBFFT_OK;
 }
 
 // ------------------------------------------------------------- plan cache

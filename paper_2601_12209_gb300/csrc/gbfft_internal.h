@@ -69,11 +69,13 @@ struct StageDesc {
 };
 
 // Control block of one persistent launch (device memory, zeroed before each launch).
+// The first two words persist across launches until read; a persistent
+// launch clears `ticket`, `abort` and the counters that follow the struct.
 struct Control {
-  unsigned int ticket;
   int error;         // first device-side error code (0 = none)
-  int abort;         // set with the error so other CTAs stop taking tickets
   int pad;
+  unsigned int ticket;
+  int abort;         // set with the error so other CTAs stop taking tickets
 };
 
 constexpr int kMaxStages = 5;

@@ -300,3 +300,25 @@ def test_exec_host_end_to_end(gb):
     out = torch.empty_like(x).pin_memory()
     plan.exec_host(abi.GBFFT_OP_FORWARD, x, out)
     assert err("exec_host fwd", out.numpy(), oracle.fft3(x.numpy())) < TOL
+
+
+@pytest.mark.parametrize("kind,shape", [("c2c", (64, 48, 32)), ("r2c", (64, 64, 64)), ("c2c", (128, 128, 128))])
+def test_autotuned_plan(gb, kind, shape):
+    """The autotuner times the variants and keeps one; results stay within tolerance,
+    and per-launch timing inside exec reports one segment per launch."""
+    from paper_2601_12209_gb300 import abi
+    nx, ny, nz = shape
+    plan = gb.Plan(nx, ny, nz, kind=kind)
+    t = plan.autotune()
+    assert all(v["tuned"] and v["ms"] > 0 for v in t.values())
+    x = synth.uniform_complex((nz, ny, nx), seed=91) if kind == "c2c" else synth.normal_real((nz, ny, nx), 92)
+    abi.gbfft_plan_time_stages(plan.handle, True)
+    X = plan.forward(x.to(dev()))
+    xr = plan.inverse(X)
+    abi.gbfft_plan_time_stages(plan.handle, False)
+    seg, ncalls = abi.gbfft_plan_stage_times(plan.handle, 0)
+    assert ncalls == 1 and len(seg) == (1 if t["forward"]["persistent"] else 3) and all(v > 0 for v in seg)
+    ref = oracle.fft3(x.numpy()) if kind == "c2c" else oracle.rfft3(x.numpy())
+    assert err(f"autotuned {kind} {shape} fwd {t['forward']}", X.cpu().numpy(), ref) < TOL
+    assert err(f"autotuned {kind} {shape} roundtrip", xr.cpu().numpy(), x.numpy()) < TOL
+    assert plan.device_error() == 0
