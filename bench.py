@@ -234,9 +234,13 @@ def main():
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--launch", default="auto", choices=["auto", "persistent", "staged"],
+                    help="auto: autotune the plan; persistent / staged: fix the launch choice")
+    ap.add_argument("--tma-mask-fwd", type=int, default=0, help="with --launch staged: tensor-copy stages (bits)")
+    ap.add_argument("--tma-mask-inv", type=int, default=0, help="with --launch staged: tensor-copy stages (bits)")
     ap.add_argument("--ncu-case", default=None,
-                    help="run one 512^3 case for a profiler and exit: staged_r2c, persistent_r2c, staged_c2c, "
-                         "persistent_c2c, slab_c2c, slab_r2c")
+                    help="run one 512^3 case for a profiler and exit: staged_r2c, staged_lsu_r2c, persistent_r2c, "
+                         "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -268,7 +272,13 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
     plan = gb.Plan(N, N, N, kind="r2c")
-    tuning = plan.autotune(stream)  # picks per-stage kernels or the persistent launch (outside the timed region)
+    if args.launch == "auto":
+        tuning = plan.autotune(stream)  # picks per-stage kernels or the persistent launch (outside the timed region)
+    else:  # a fixed choice, e.g. to profile exactly what an earlier autotuned run chose
+        for k, (pers, mask) in enumerate(((args.launch == "persistent", args.tma_mask_fwd),
+                                          (args.launch == "persistent", args.tma_mask_inv))):
+            abi.gbfft_plan_set_tuning(plan.handle, k, pers, mask)
+        tuning = {name: abi.gbfft_plan_get_tuning(plan.handle, k) for k, name in enumerate(("forward", "inverse"))}
     r = synth.normal_real((N, N, N), seed=2).to(dev)
     spec = torch.empty((1, N, N, N // 2 + 1), dtype=torch.complex64, device=dev)
     real_out = torch.empty((1, N, N, N), dtype=torch.float32, device=dev)
@@ -408,7 +418,8 @@ def ncu_case(name):
     from paper_2601_12209_gb300 import _build, abi
     _build.build()
     kind = "r2c" if name.endswith("r2c") else "c2c"
-    plan = gb.Plan(N, N, N, kind=kind, staged=name.startswith("staged"), slab=name.startswith("slab"))
+    plan = gb.Plan(N, N, N, kind=kind, staged=name.startswith("staged"), slab=name.startswith("slab"),
+                   tma="_lsu" not in name)
     x = (synth.normal_real((N, N, N), seed=2) if kind == "r2c" else synth.uniform_complex((N, N, N), seed=3)).cuda()
     for _ in range(3):
         y = plan.exec(abi.GBFFT_OP_FORWARD, x)

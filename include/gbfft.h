@@ -164,6 +164,13 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
 int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask, float* ms,
                           float* stage_ms);
 /*
+ * Fix a pipeline's launch choice by hand (as gbfft_plan_autotune would):
+ * persistent 1 = one persistent launch (when a kernel family exists), else
+ * staged launches with bit s of tma_mask selecting the tensor-copy kernel for
+ * stage s (where it applies).
+ */
+int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask);
+/*
  * Per-launch timing inside exec calls: while enabled, each exec records a
  * CUDA event on its stream before its first launch and after every launch.
  * gbfft_plan_stage_times synchronises on the recorded events of `pipeline`,

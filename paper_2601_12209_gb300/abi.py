@@ -48,6 +48,7 @@ EXPORTED = (
     "gbfft_get_device_error", "gbfft_debug_run", "gbfft_strerror", "gbfft_plan_destroy",
     "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version", "gbfft_exec_c2c_noalloc",
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
+    "gbfft_plan_set_tuning",
 )
 
 _lib = None
@@ -97,6 +98,7 @@ def load() -> ctypes.CDLL:
             "gbfft_plan_get_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(u),
                                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
             "gbfft_plan_time_stages": (i, [vp, i]),
+            "gbfft_plan_set_tuning": (i, [vp, i, i, u]),
             "gbfft_plan_stage_times": (i, [vp, i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i),
                                            ctypes.POINTER(i)]),
         }
@@ -231,6 +233,10 @@ def gbfft_plan_get_tuning(plan: int, pipeline: int) -> dict:
           ctypes.byref(mask), ctypes.byref(ms), stage)
     return {"tuned": bool(tuned.value), "persistent": bool(pers.value), "tma_mask": mask.value, "ms": ms.value,
             "stage_ms": [stage[k] for k in range(5)]}
+
+
+def gbfft_plan_set_tuning(plan: int, pipeline: int, persistent: bool, tma_mask: int) -> None:
+    _call("gbfft_plan_set_tuning", ctypes.c_void_p(plan), int(pipeline), int(bool(persistent)), int(tma_mask))
 
 
 def gbfft_plan_time_stages(plan: int, enable: bool) -> None:

@@ -1149,6 +1149,17 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   return GBFFT_OK;
 }
 
+int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask) {
+  if (!plan || pipeline < 0 || pipeline > 2) return GBFFT_ERR_INVALID_ARG;
+  gbfft_plan_s::Tuning& t = plan->tune[pipeline];
+  t.tuned = true;
+  t.persistent = persistent != 0;
+  t.tma_mask = tma_mask;
+  t.ms = 0.f;
+  for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;
+  return GBFFT_OK;
+}
+
 int gbfft_plan_time_stages(gbfft_plan plan, int enable) {
   if (!plan) return GBFFT_ERR_INVALID_ARG;
   plan->time_stages = enable != 0;
