@@ -84,7 +84,7 @@ def kernel_source_hash():
 
 def ncu_traffic(kernel_key):
     """Per-launch DRAM bytes from the committed ncu summary, if taken on the current kernels."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    p = os.path.join(ROOT, "profiles", "ncu_traffic_r2c_512.json")
     if not os.path.exists(p):
         return None
     try:
@@ -149,6 +149,19 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def reduce_max_ms(dist, ms: float, device) -> float:
+    """Max of a per-rank time over all ranks (the slowest replica sets the job time)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, flops_per_step: float, ms_per_step: float) -> float:
+    """GFLOP/s of the whole job: every replica does one step's work per ms_per_step."""
+    return world * flops_per_step / (ms_per_step * 1e-3) / 1e9
 
 
 def dist_setup(args):
@@ -322,12 +335,10 @@ def main():
     fwd_ms = [evs[2 * s].elapsed_time(evs[2 * s + 1]) for s in range(args.steps)]
     inv_ms = [evs[2 * s + 1].elapsed_time(evs[2 * s + 2]) for s in range(args.steps)]
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max_ms(dist, total_ms, dev)
     ms_per_step = total_ms / args.steps
     flops_step = 2 * flops_5n(N, N, N)
-    value = world * flops_step / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_value(world, flops_step, ms_per_step)
     err = plan.device_error()
 
     # roofline of the dominant launch: per-launch CUDA events recorded by the
