@@ -439,6 +439,71 @@ def ncu_case(name):
     assert plan.device_error() == 0
 
 
+def batched_variant(torch, gb, abi, stream, steps, warmup):
+    """64 uneven C2C grids: one graph-captured batched launch vs one plan per grid (forward)."""
+    import synth
+    shapes, grids = synth.batched_grids(64, seed=6)
+    m = gb.ManyPlan(shapes)
+    x = m.pack([g.cuda() for g in grids])
+    y = m.empty()
+    npts = sum(nx * ny * nz for (nx, ny, nz) in shapes)
+    flops = sum(flops_5n(*s) for s in shapes)
+    alg_bytes = 48 * npts
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
+            m.exec_separate(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
+    res = {"grids": 64, "points": npts, "largest_smallest_ratio": max(a * b * c for a, b, c in shapes)
+           / min(a * b * c for a, b, c in shapes)}
+    for name, fn in (("one_launch_graph", lambda: graph.replay()),
+                     ("one_launch", lambda: m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)),
+                     ("separate_plans", lambda: m.exec_separate(abi.GBFFT_OP_FORWARD, x, y, stream=stream))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9}
+    res["device_error"] = m.device_error()
+    m.close()
+    return res
+
+
+def poisson_variant(torch, gb, abi, stream, steps, warmup):
+    """Periodic Poisson solve on 256^3 (R2C, multiplier fused into the z stage, C2R)."""
+    import synth
+    n = 256
+    f, _ = synth.poisson_rhs(n, seed=4)
+    f = f.cuda()
+    p = gb.Plan(n, n, n, kind="r2c")
+    tune = p.autotune(stream)
+    phi = torch.empty_like(f)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            p.poisson(f, phi, stream=stream)
+        e0.record(stream)
+        for _ in range(steps):
+            p.poisson(f, phi, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    nc = (n // 2 + 1) * n * n
+    alg = 2 * (4 * n ** 3 + 8 * nc) + 2 * 16 * nc + 16 * nc  # x, y out and back; fused z: one read + one write
+    out = {"ms": ms, "alg_gbs": alg / (ms * 1e-3) / 1e9, "tuning": tune["poisson"]}
+    p.close()
+    return out
+
+
 def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
     """C2C 512^3 pencil and slab, R2C slab, forward+adjoint: per-launch medians."""
     import synth
@@ -489,6 +554,8 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
         out["c2c_512_pencil_staged_" + ("tma" if tma else "lsu") + "_fwd_inv_ms"] = med[0] + med[1]
         ps.close()
     del x
+    out["batched_64"] = batched_variant(torch, gb, abi, stream, steps, warmup)
+    out["poisson_256"] = poisson_variant(torch, gb, abi, stream, steps, warmup)
     # cuFFT via torch.fft on the same GPU: context only, not a target
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(warmup):

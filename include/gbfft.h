@@ -238,6 +238,30 @@ int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* 
 #define GBFFT_NOALLOC_MAX_POINTS 4194304
 int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void* in, void* out, void* stream);
 
+/*
+ * Batched grids (the paper's task graph over many chunks of uneven cost,
+ * Sections III-C and IV-D, Table II): `count` C2C FP32 grids of different
+ * sizes (dims[3g..3g+2] = nx, ny, nz of grid g; each length 2^a 3^b 5^c in
+ * 32..256) transformed by ONE persistent launch whose blocks take the tiles of
+ * every grid from one ticket counter (stage-major across grids, bounded
+ * per-grid dependency waits). The grids are packed back to back in `in` and
+ * `out` (grid g starts at element offset gbfft_many_layout(g); every grid
+ * starts 16-byte aligned). The launch needs only in/out and plan-owned
+ * memory, so it can be captured in a CUDA graph and replayed. count <= 85.
+ * flags: 0 or GBFFT_DEBUG_TIMEOUT.
+ */
+typedef struct gbfft_many_s* gbfft_many;
+int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flags);
+/* Element offset of grid `grid` and the total complex elements of the packed buffers. */
+int gbfft_many_layout(gbfft_many m, int grid, long long* offset, long long* total);
+/* One persistent launch for all grids; op GBFFT_OP_FORWARD or GBFFT_OP_INVERSE (1/N per grid). */
+int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* stream);
+/* The same transforms as one plan per grid, launched one after another (for comparison). */
+int gbfft_many_exec_separate(gbfft_many m, int op, const void* in, void* out, void* stream);
+/* Read and clear the device error word of the batched launches (synchronises). */
+int gbfft_many_get_device_error(gbfft_many m, int* code);
+void gbfft_many_destroy(gbfft_many m);
+
 /* Human-readable name of an error code (static storage). */
 const char* gbfft_strerror(int code);
 

@@ -22,7 +22,7 @@ from . import abi
 from .abi import (GBFFT_C2C, GBFFT_R2C, GBFFT_OP_FORWARD, GBFFT_OP_INVERSE, GBFFT_OP_ADJOINT,  # noqa: F401
                   GBFFT_OP_INVERSE_ADJOINT, GbfftError)
 
-__all__ = ["Plan", "fftn", "ifftn", "rfftn", "irfftn", "poisson", "FFT3", "RFFT3", "IRFFT3", "Poisson",
+__all__ = ["Plan", "ManyPlan", "fftn", "ifftn", "rfftn", "irfftn", "poisson", "FFT3", "RFFT3", "IRFFT3", "Poisson",
            "abi", "GbfftError"]
 
 
@@ -164,6 +164,55 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None) and not self._cached:
             abi.gbfft_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ManyPlan:
+    """Many C2C grids of different sizes, transformed by one persistent launch.
+
+    shapes: list of (nx, ny, nz). Data is packed back to back (pack/unpack helpers
+    below); exec() runs one launch (capturable in a CUDA graph), exec_separate()
+    one plan per grid for comparison.
+    """
+
+    def __init__(self, shapes, debug_timeout: bool = False):
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.handle = abi.gbfft_many_create(self.shapes, abi.GBFFT_DEBUG_TIMEOUT if debug_timeout else 0)
+        self.offsets = [abi.gbfft_many_layout(self.handle, g)[0] for g in range(len(self.shapes))]
+        self.total = abi.gbfft_many_layout(self.handle, 0)[1]
+
+    def empty(self, device="cuda") -> torch.Tensor:
+        return torch.zeros(self.total, dtype=torch.complex64, device=device)
+
+    def pack(self, grids, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self.empty(grids[0].device) if out is None else out
+        for (nx, ny, nz), off, g in zip(self.shapes, self.offsets, grids):
+            out[off:off + nx * ny * nz].copy_(g.reshape(-1))
+        return out
+
+    def unpack(self, packed: torch.Tensor):
+        return [packed[off:off + nx * ny * nz].view(nz, ny, nx) for (nx, ny, nz), off in zip(self.shapes, self.offsets)]
+
+    def exec(self, op: int, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        abi.gbfft_many_exec(self.handle, int(op), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def exec_separate(self, op: int, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        abi.gbfft_many_exec_separate(self.handle, int(op), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def device_error(self) -> int:
+        return abi.gbfft_many_get_device_error(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.gbfft_many_destroy(self.handle)
         self.handle = None
 
     def __del__(self):

@@ -48,7 +48,8 @@ EXPORTED = (
     "gbfft_get_device_error", "gbfft_debug_run", "gbfft_strerror", "gbfft_plan_destroy",
     "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version", "gbfft_exec_c2c_noalloc",
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
-    "gbfft_plan_set_tuning",
+    "gbfft_plan_set_tuning", "gbfft_many_create", "gbfft_many_layout", "gbfft_many_exec",
+    "gbfft_many_exec_separate", "gbfft_many_get_device_error", "gbfft_many_destroy",
 )
 
 _lib = None
@@ -99,6 +100,12 @@ def load() -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
             "gbfft_plan_time_stages": (i, [vp, i]),
             "gbfft_plan_set_tuning": (i, [vp, i, i, u]),
+            "gbfft_many_create": (i, [plan_p, i, ctypes.POINTER(i), u]),
+            "gbfft_many_layout": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+            "gbfft_many_exec": (i, [vp, i, vp, vp, vp]),
+            "gbfft_many_exec_separate": (i, [vp, i, vp, vp, vp]),
+            "gbfft_many_get_device_error": (i, [vp, ctypes.POINTER(i)]),
+            "gbfft_many_destroy": (None, [vp]),
             "gbfft_plan_stage_times": (i, [vp, i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i),
                                            ctypes.POINTER(i)]),
         }
@@ -249,6 +256,40 @@ def gbfft_plan_stage_times(plan: int, pipeline: int) -> tuple[list[float], int]:
     _call("gbfft_plan_stage_times", ctypes.c_void_p(plan), int(pipeline), avg, ctypes.byref(nseg),
           ctypes.byref(ncalls))
     return [avg[k] for k in range(nseg.value)], ncalls.value
+
+
+def gbfft_many_create(shapes, flags: int = 0) -> int:
+    """shapes: list of (nx, ny, nz)."""
+    dims = (ctypes.c_int * (3 * len(shapes)))(*[int(v) for sh in shapes for v in sh])
+    h = ctypes.c_void_p()
+    _call("gbfft_many_create", ctypes.byref(h), len(shapes), dims, int(flags))
+    return h.value
+
+
+def gbfft_many_layout(m: int, grid: int) -> tuple[int, int]:
+    off, tot = ctypes.c_longlong(), ctypes.c_longlong()
+    _call("gbfft_many_layout", ctypes.c_void_p(m), int(grid), ctypes.byref(off), ctypes.byref(tot))
+    return off.value, tot.value
+
+
+def gbfft_many_exec(m: int, op: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("gbfft_many_exec", ctypes.c_void_p(m), int(op), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_many_exec_separate(m: int, op: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("gbfft_many_exec_separate", ctypes.c_void_p(m), int(op), ctypes.c_void_p(in_ptr),
+          ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
+
+
+def gbfft_many_get_device_error(m: int) -> int:
+    c = ctypes.c_int()
+    _call("gbfft_many_get_device_error", ctypes.c_void_p(m), ctypes.byref(c))
+    return c.value
+
+
+def gbfft_many_destroy(m: int) -> None:
+    load().gbfft_many_destroy(ctypes.c_void_p(m))
 
 
 def raw_rc(name: str, *args) -> int:

@@ -15,6 +15,7 @@
 
 #include "../../include/gbfft.h"
 #include "gbfft_kernels.cuh"
+#include "gbfft_many.cuh"
 
 namespace gbfft {
 
@@ -540,7 +541,8 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags 
   int bpsm = 1;
   cudaError_t e = launch_info(k->fn, k->threads, k->smem, &bpsm);
   if (e != cudaSuccess) return GBFFT_ERR_CUDA;
-  long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
+  if (!k->loops && d.n_tiles > 0x7FFFFFFFLL) return GBFFT_ERR_INVALID_ARG;
+  long long grid = k->loops ? std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm) : d.n_tiles;
   StageDesc dd = d;
   void* args[] = {&dd};
   e = cudaLaunchKernel(k->fn, dim3((unsigned)grid), dim3((unsigned)k->threads), args, k->smem, stream);
@@ -1230,5 +1232,253 @@ void gbfft_plan_cache_clear(void) {
   for (auto& kv : g_cache) free_plan(kv.second);
   g_cache.clear();
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------- batched grids
+
+namespace gbfft {
+void register_many_group_0(std::vector<ManyKernel>&);
+void register_many_group_1(std::vector<ManyKernel>&);
+std::vector<ManyKernel>& many_registry() {
+  static std::vector<ManyKernel> v;
+  return v;
+}
+static std::once_flag g_many_once;
+static const ManyKernel* find_many(const std::vector<int>& codes) {
+  std::call_once(g_many_once, [] {
+    register_many_group_0(many_registry());
+    register_many_group_1(many_registry());
+  });
+  for (const auto& k : many_registry()) {
+    bool all = true;
+    for (int c : codes) {
+      bool f = false;
+      for (int i = 0; i < k.ncodes; ++i) f |= k.codes[i] == c;
+      all &= f;
+    }
+    if (all) return &k;
+  }
+  return nullptr;
+}
+}  // namespace gbfft
+
+struct gbfft_many_s {
+  int count = 0, device = 0;
+  unsigned flags = 0;
+  std::vector<gbfft_plan> plans;  // one per grid: twiddles, and the separate-launch path
+  std::vector<long long> offs;    // element offset of each grid in the packed buffers
+  long long total = 0;            // complex elements of all grids
+  ManySegment* segs[2] = {nullptr, nullptr};  // forward, inverse
+  unsigned int* first[2] = {nullptr, nullptr};
+  unsigned int tiles[2] = {0, 0};
+  int nseg = 0;
+  const ManyKernel* kern[2] = {nullptr, nullptr};
+  void* ws = nullptr;
+  Control* ctl = nullptr;
+  unsigned int* counters = nullptr;
+  size_t counter_words = 0;
+};
+
+static void free_many(gbfft_many_s* m) {
+  if (!m) return;
+  for (auto p : m->plans) free_plan(p);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(m->segs[i]);
+    cudaFree(m->first[i]);
+  }
+  cudaFree(m->ws);
+  cudaFree(m->ctl);
+  delete m;
+}
+
+extern "C" {
+
+int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flags) {
+  if (!out) return GBFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || 3 * count > kManyMaxSegs || !dims) return GBFFT_ERR_INVALID_ARG;
+  if (flags & ~(unsigned)GBFFT_DEBUG_TIMEOUT) return GBFFT_ERR_INVALID_ARG;
+  gbfft_many_s* m = new gbfft_many_s();
+  m->count = count;
+  m->flags = flags;
+  cudaGetDevice(&m->device);
+  std::vector<ManySegment> segs[2];
+  std::vector<unsigned int> first[2];
+  size_t words = 0;
+  std::vector<int> codes[2];
+  for (int g = 0; g < count; ++g) {
+    gbfft_plan p = nullptr;
+    int rc = gbfft_plan_create(&p, dims[3 * g], dims[3 * g + 1], dims[3 * g + 2], GBFFT_C2C, GBFFT_FP32, 1,
+                               GBFFT_STAGED | (flags & GBFFT_DEBUG_TIMEOUT));
+    if (rc) {
+      free_many(m);
+      return rc;
+    }
+    m->plans.push_back(p);
+    m->offs.push_back(m->total);
+    long long n = (long long)dims[3 * g] * dims[3 * g + 1] * dims[3 * g + 2];
+    m->total += (n + 1) / 2 * 2;  // keep every grid 16-byte aligned
+  }
+  // segments stage-major: every grid's first stage, then second, then third
+  for (int pipe = 0; pipe < 2; ++pipe) {
+    const int op = pipe == 0 ? GBFFT_OP_FORWARD : GBFFT_OP_INVERSE;
+    std::vector<Pipeline> P(count);
+    const Buf none{nullptr, -1};
+    for (int g = 0; g < count; ++g) {
+      // every stage of grid g must stay inside grid g's slice of the packed buffers
+      const long long ng = (long long)dims[3 * g] * dims[3 * g + 1] * dims[3 * g + 2];
+      char* fake = reinterpret_cast<char*>(16);  // non-null placeholder, never dereferenced
+      const Buf b{fake, ng};
+      Pipeline chk = build_pipeline(m->plans[g], pipe, op, b, b, b, b);
+      if (validate(chk) != GBFFT_OK) {
+        free_many(m);
+        return GBFFT_ERR_INVALID_ARG;
+      }
+      P[g] = build_pipeline(m->plans[g], pipe, op, none, none, none, none);
+    }
+    const int roles[3][2] = {{0, 1}, {1, 2}, {2, 1}};  // C2C pencil: in->out, out->ws, ws->out
+    std::vector<long long> seg_index(3 * count);
+    unsigned int acc = 0;
+    for (int k = 0; k < 3; ++k)
+      for (int g = 0; g < count; ++g) {
+        ManySegment s;
+        std::memset(&s, 0, sizeof(s));
+        s.d = P[g].st[k];
+        s.d.in = nullptr;
+        s.d.out = nullptr;
+        s.in_buf = roles[k][0];
+        s.out_buf = roles[k][1];
+        s.in_off = m->offs[g];
+        s.out_off = m->offs[g];
+        s.c_outer = (long long)words;
+        words += (size_t)s.d.batch * s.d.n_outer;
+        s.c_outer16 = (long long)words;
+        words += (size_t)s.d.batch * gchunks(s.d.n_outer);
+        s.c_gchunk = (long long)words;
+        words += (size_t)s.d.batch * s.d.n_gchunks;
+        s.c_total = (long long)words;
+        words += (size_t)s.d.batch;
+        s.c_stage = (long long)words;
+        words += 1;
+        s.p_outer = s.p_outer16 = s.p_gchunk = s.p_total = s.p_stage = -1;
+        s.prev_tiles = 0;
+        if (k > 0) {
+          const ManySegment& q = segs[pipe][(size_t)(k - 1) * count + g];
+          s.p_outer = q.c_outer;
+          s.p_outer16 = q.c_outer16;
+          s.p_gchunk = q.c_gchunk;
+          s.p_total = q.c_total;
+          s.p_stage = q.c_stage;
+          s.prev_tiles = q.d.n_tiles;
+        }
+        first[pipe].push_back(acc);
+        acc += (unsigned int)s.d.n_tiles;
+        segs[pipe].push_back(s);
+        const int code = kcode(s.d.L, s.d.kind, s.d.dir);
+        if (std::find(codes[pipe].begin(), codes[pipe].end(), code) == codes[pipe].end())
+          codes[pipe].push_back(code);
+      }
+    first[pipe].push_back(acc);
+    m->tiles[pipe] = acc;
+    m->kern[pipe] = find_many(codes[pipe]);
+    if (!m->kern[pipe]) {
+      free_many(m);
+      return GBFFT_ERR_UNSUPPORTED_SIZE;
+    }
+  }
+  m->nseg = 3 * count;
+  m->counter_words = words;  // forward and inverse counters are laid out side by side
+  bool ok = true;
+  for (int pipe = 0; pipe < 2 && ok; ++pipe) {
+    ok = cudaMalloc(&m->segs[pipe], segs[pipe].size() * sizeof(ManySegment)) == cudaSuccess &&
+         cudaMemcpy(m->segs[pipe], segs[pipe].data(), segs[pipe].size() * sizeof(ManySegment),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMalloc(&m->first[pipe], first[pipe].size() * sizeof(unsigned int)) == cudaSuccess &&
+         cudaMemcpy(m->first[pipe], first[pipe].data(), first[pipe].size() * sizeof(unsigned int),
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  void* c = nullptr;
+  ok = ok && cudaMalloc(&m->ws, (size_t)m->total * sizeof(float2)) == cudaSuccess &&
+       cudaMalloc(&c, sizeof(Control) + m->counter_words * sizeof(unsigned int)) == cudaSuccess &&
+       cudaMemset(c, 0, sizeof(Control) + m->counter_words * sizeof(unsigned int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (c) cudaFree(c);
+    free_many(m);
+    return GBFFT_ERR_ALLOC;
+  }
+  m->ctl = reinterpret_cast<Control*>(c);
+  m->counters = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(c) + sizeof(Control));
+  *out = m;
+  return GBFFT_OK;
+}
+
+int gbfft_many_layout(gbfft_many m, int grid, long long* offset, long long* total) {
+  if (!m || grid < 0 || grid >= m->count) return GBFFT_ERR_INVALID_ARG;
+  if (offset) *offset = m->offs[grid];
+  if (total) *total = m->total;
+  return GBFFT_OK;
+}
+
+int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* stream) {
+  if (!m || (op != GBFFT_OP_FORWARD && op != GBFFT_OP_INVERSE)) return GBFFT_ERR_INVALID_ARG;
+  int rc = check_ptrs(in, out);
+  if (rc) return rc;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  const int pipe = op == GBFFT_OP_FORWARD ? 0 : 1;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ManyArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.segs = m->segs[pipe];
+  a.first = m->first[pipe];
+  a.nseg = m->nseg;
+  a.total = m->tiles[pipe];
+  a.in = reinterpret_cast<const float2*>(in);
+  a.out = reinterpret_cast<float2*>(out);
+  a.ws = reinterpret_cast<float2*>(m->ws);
+  a.ctl = m->ctl;
+  a.counters = m->counters;
+  const bool dbg = (m->flags & GBFFT_DEBUG_TIMEOUT) != 0;
+  a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
+  a.debug_never = dbg ? 1 : 0;
+  cudaError_t e = cudaMemsetAsync(&m->ctl->ticket, 0,
+                                  2 * sizeof(unsigned int) + m->counter_words * sizeof(unsigned int), st);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  const ManyKernel* k = m->kern[pipe];
+  int bpsm = 1;
+  e = launch_info(k->fn, kManyThreads, k->smem, &bpsm);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  (void)bpsm;
+  // one block per ticket (tile); blocks start in ticket order
+  void* args[] = {&a};
+  e = cudaLaunchKernel(k->fn, dim3((unsigned)std::max<unsigned>(a.total, 1u)), dim3(kManyThreads), args, k->smem, st);
+  return cuda_err(e);
+}
+
+int gbfft_many_exec_separate(gbfft_many m, int op, const void* in, void* out, void* stream) {
+  if (!m || (op != GBFFT_OP_FORWARD && op != GBFFT_OP_INVERSE)) return GBFFT_ERR_INVALID_ARG;
+  int rc = check_ptrs(in, out);
+  if (rc) return rc;
+  for (int g = 0; g < m->count; ++g) {
+    rc = gbfft_exec(m->plans[g], op, reinterpret_cast<const float2*>(in) + m->offs[g],
+                    reinterpret_cast<float2*>(out) + m->offs[g], stream);
+    if (rc) return rc;
+  }
+  return GBFFT_OK;
+}
+
+int gbfft_many_get_device_error(gbfft_many m, int* code) {
+  if (!m || !code) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GBFFT_ERR_CUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, &m->ctl->error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GBFFT_ERR_CUDA;
+  *code = e == kDevErrTimeout ? GBFFT_ERR_TIMEOUT : (e ? GBFFT_ERR_CUDA : GBFFT_OK);
+  if (cudaMemset(&m->ctl->error, 0, sizeof(int)) != cudaSuccess) return GBFFT_ERR_CUDA;
+  return GBFFT_OK;
+}
+
+void gbfft_many_destroy(gbfft_many m) { free_many(m); }
 
 }  // extern "C"

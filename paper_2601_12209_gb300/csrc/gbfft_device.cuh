@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "gbfft_internal.h"
 
 namespace gbfft {
@@ -267,6 +269,16 @@ __device__ __forceinline__ void dft(float2* a) {
   else if constexpr (R == 16) dft16<DIR>(a);
 }
 
+// Thread index read through a volatile instruction: the per-tile functions
+// use it instead of threadIdx.x so the compiler cannot hoist their
+// tile-invariant shared-memory addresses out of the tile loop of a kernel
+// (for mixed-radix lengths that hoisting exhausts the registers).
+__device__ __forceinline__ int tid_x() {
+  int t;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t) : : "memory");
+  return t;
+}
+
 // ------------------------------------------------------------ memory helpers
 
 // Tile layout in shared memory: element n of pencil p at n*16 + swizzled p.
@@ -292,7 +304,7 @@ struct TileIO {
 // along n (coalesced), each lane moves one pencil pair as a 16-byte smem chunk.
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_load(float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
+  for (int it = tid_x(); it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
@@ -306,7 +318,7 @@ template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
   const float sc = io.scale;
   const bool unit = sc == 1.f;
-  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
+  for (int it = tid_x(); it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float4 v = *reinterpret_cast<const float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1)));
@@ -320,7 +332,7 @@ __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
 // along p, so 16 lanes move one 128-byte line.
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
+  for (int it = tid_x(); it < NROWS * 16; it += THREADS) {
     int p = it & 15, n = it >> 4;
     float2 a = make_float2(0.f, 0.f);
     if (p < io.valid) a = ld_data(io.gin + p + n * io.in_n);
@@ -330,7 +342,7 @@ __device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
 
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void col_store(const float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
+  for (int it = tid_x(); it < NROWS * 16; it += THREADS) {
     int p = it & 15, n = it >> 4;
     if (p < io.valid) {
       float2 v = sm[swz(n, p)];
@@ -353,6 +365,20 @@ __device__ __forceinline__ int rowbox_index(int n, int p) {
   return ((n >> 4) << 8) | (p << 4) | ((((n & 15) >> 1) ^ (p & 7)) << 1) | (n & 1);
 }
 
+// Compile-time loop: f(integral_constant<int, 0>) ... f(integral_constant<int, N-1>).
+// The butterfly loops use it so every register array index is a constant by
+// construction (with #pragma unroll alone, the compiler keeps some of these
+// loops rolled inside kernels that loop over tiles, and the arrays go to
+// local memory).
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, bool SYNC_BEFORE_WRITE,
           int SRC_LAYOUT = 0>
 __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, const TileIO& io) {
@@ -362,14 +388,15 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
   constexpr int NB = L / R;
   constexpr int G = THREADS / 16;
   constexpr int NBT = (NB + G - 1) / G;
-  const int p = threadIdx.x & 15, g = threadIdx.x >> 4;
+  constexpr int TWO = tw_pass_offset(L, PASS);  // evaluated at compile time
+  const int p = tid_x() & 15, g = tid_x() >> 4;
   float2 v[NBT][R];
-#pragma unroll
-  for (int t = 0; t < NBT; ++t) {
+  static_for<NBT>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
     const int j = g + t * G;
     if (NB % G == 0 || j < NB) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
+      static_for<R>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
         const int n = j + r * NB;
         if constexpr (SRC_GLOBAL) {
           v[t][r] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
@@ -378,55 +405,64 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
         } else {
           v[t][r] = sm[swz(n, p)];
         }
-      }
+      });
       if constexpr (Ns > 1) {
         const int k = j % Ns;
         // tw is 16-byte aligned and every offset below is even when R is even
-        const float2* twp = tw + tw_pass_offset(L, PASS) + k * R;
+        const float2* twp = tw + TWO + k * R;
         if constexpr (R % 2 == 0) {
-#pragma unroll
-          for (int r = 0; r < R; r += 2) {
+          static_for<R / 2>([&](auto hc) {
+            constexpr int r = 2 * decltype(hc)::value;
             const float4 w = *reinterpret_cast<const float4*>(twp + r);
-            if (r > 0) v[t][r] = cmul(v[t][r], tw_dir<DIR>(make_float2(w.x, w.y)));
+            if constexpr (r > 0) v[t][r] = cmul(v[t][r], tw_dir<DIR>(make_float2(w.x, w.y)));
             v[t][r + 1] = cmul(v[t][r + 1], tw_dir<DIR>(make_float2(w.z, w.w)));
-          }
+          });
         } else {
-#pragma unroll
-          for (int r = 1; r < R; ++r) v[t][r] = cmul(v[t][r], tw_dir<DIR>(twp[r]));
+          static_for<R - 1>([&](auto rc) {
+            constexpr int r = decltype(rc)::value + 1;
+            v[t][r] = cmul(v[t][r], tw_dir<DIR>(twp[r]));
+          });
         }
       }
       dft<R, DIR>(v[t]);
     }
-  }
+  });
   if constexpr (DST_GLOBAL) {
     if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
     const bool unit = io.scale == 1.f;
-#pragma unroll
-    for (int t = 0; t < NBT; ++t) {
+    const long long step = (long long)NB * io.out_n;  // last pass: Ns R = L, outputs j + q NB
+    static_for<NBT>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
       const int j = g + t * G;
       if ((NB % G == 0 || j < NB) && p < io.valid) {
         float2* o = io.gout + p + (long long)j * io.out_n;
-        const long long step = (long long)NB * io.out_n;  // last pass: Ns R = L, outputs j + q NB
         if (unit) {
-#pragma unroll
-          for (int q = 0; q < R; ++q) st_data(o + q * step, v[t][q]);
+          static_for<R>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            st_data(o + q * step, v[t][q]);
+          });
         } else {
-#pragma unroll
-          for (int q = 0; q < R; ++q) st_data(o + q * step, cscale(v[t][q], io.scale));
+          static_for<R>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            st_data(o + q * step, cscale(v[t][q], io.scale));
+          });
         }
       }
-    }
+    });
   } else {
     if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
-#pragma unroll
-    for (int t = 0; t < NBT; ++t) {
+    static_for<NBT>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
       const int j = g + t * G;
       if (NB % G == 0 || j < NB) {
         const int k = j % Ns;
-#pragma unroll
-        for (int q = 0; q < R; ++q) sm[swz((j - k) * R + k + q * Ns, p)] = v[t][q];
+        const int base = (j - k) * R + k;
+        static_for<R>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          sm[swz(base + q * Ns, p)] = v[t][q];
+        });
       }
-    }
+    });
     __syncthreads();
   }
 }
@@ -459,7 +495,7 @@ __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const T
 template <int M, int THREADS>
 __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float interior) {
   constexpr int NPAIR = M / 2 + 1;
-  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+  for (int it = tid_x(); it < NPAIR * 16; it += THREADS) {
     const int p = it & 15, k = it >> 4;
     if (k == 0) {
       float2 z0 = sm[swz(0, p)];
@@ -489,7 +525,7 @@ __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float in
 template <int M, int THREADS>
 __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float interior) {
   constexpr int NPAIR = M / 2 + 1;
-  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+  for (int it = tid_x(); it < NPAIR * 16; it += THREADS) {
     const int p = it & 15, k = it >> 4;
     if (k == 0) {
       float a = sm[swz(0, p)].x, c = sm[swz(M, p)].x;
@@ -515,7 +551,7 @@ __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float int
 template <int L, int THREADS>
 __device__ __forceinline__ void poisson_multiply(float2* sm, int gfirst, int ky_idx, int ny, float inv_n) {
   const float ky = (float)(ky_idx <= ny / 2 ? ky_idx : ky_idx - ny);
-  for (int it = threadIdx.x; it < L * 16; it += THREADS) {
+  for (int it = tid_x(); it < L * 16; it += THREADS) {
     const int p = it & 15, n = it >> 4;
     const float kx = (float)(gfirst + p);
     const float kz = (float)(n <= L / 2 ? n : n - L);
@@ -538,10 +574,12 @@ struct TileShape {
 
 __device__ __forceinline__ TileIO make_io(const StageDesc& d, long long tile, int& o_out, int& g0_out) {
   TileIO io;
-  const long long gc = tile % d.n_gchunks;
-  const long long rest = tile / d.n_gchunks;
-  const int o = (int)(rest % d.n_outer);
-  const int b = (int)(rest / d.n_outer);
+  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
+  const unsigned t32 = (unsigned)tile;
+  const unsigned gc = t32 % (unsigned)d.n_gchunks;
+  const unsigned rest = t32 / (unsigned)d.n_gchunks;
+  const int o = (int)(rest % (unsigned)d.n_outer);
+  const int b = (int)(rest / (unsigned)d.n_outer);
   const int g0 = (int)gc * kTileP;
   io.valid = min(kTileP, d.n_group - g0);
   io.gin = d.in + b * d.in_b + o * d.in_o + g0 * d.in_g;
@@ -634,9 +672,10 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
 // Copy a stage's twiddle tables into shared memory.
 template <int L, int THREADS>
 __device__ __forceinline__ void load_twiddles(float2* tw_s, float2* tw2_s, const StageDesc& d, bool need_tw2) {
-  for (int i = threadIdx.x; i < tw_table_len(L); i += THREADS) tw_s[i] = d.tw[i];
+  constexpr int TWL = tw_table_len(L);
+  for (int i = tid_x(); i < TWL; i += THREADS) tw_s[i] = d.tw[i];
   if (need_tw2)
-    for (int i = threadIdx.x; i <= L; i += THREADS) tw2_s[i] = d.tw2[i];
+    for (int i = tid_x(); i <= L; i += THREADS) tw2_s[i] = d.tw2[i];
 }
 
 }  // namespace gbfft

@@ -15,6 +15,7 @@ struct StageKernel {
   const void* fn;
   int threads;
   size_t smem;
+  bool loops;  // grid-stride tile loop (else one tile per block)
 };
 
 struct PersistentKernel {
@@ -47,27 +48,37 @@ constexpr size_t stage_smem_bytes() {
   return sizeof(float2) * ((size_t)(L + 1) * kTileP + tw_table_len(L) + (L + 1));
 }
 
-// One launch per stage. Each block loops over tiles with a grid stride, so
-// the twiddle tables are staged into shared memory once per block.
+// Power-of-two lengths: each block loops over tiles with a grid stride, so the
+// twiddle tables are staged into shared memory once per block. Mixed-radix
+// lengths (factors 3, 5): one tile per block -- inside a tile loop the
+// compiler's register allocation of their butterflies spills, straight-line
+// it does not; the hardware block scheduler then hands out the tiles.
+__host__ __device__ constexpr bool stage_loops(int L) { return (L & (L - 1)) == 0; }
+
 template <int L, int DIR, int KIND>
 __global__ void __launch_bounds__(threads_for(L), min_blocks_for(L)) stage_kernel(StageDesc d) {
   constexpr int THREADS = threads_for(L);
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* tw = sm + (L + 1) * kTileP;
-  float2* tw2 = tw + tw_table_len(L);
+  constexpr int TWL = tw_table_len(L);
+  float2* tw2 = tw + TWL;
   load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre);
   __syncthreads();
-  for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
-    process_tile<L, DIR, KIND, THREADS>(d, tile, sm, tw, tw2);
-    __syncthreads();
+  if constexpr (stage_loops(L)) {
+    for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
+      process_tile<L, DIR, KIND, THREADS>(d, tile, sm, tw, tw2);
+      __syncthreads();
+    }
+  } else {
+    if ((long long)blockIdx.x < d.n_tiles) process_tile<L, DIR, KIND, THREADS>(d, (long long)blockIdx.x, sm, tw, tw2);
   }
 }
 
 template <int L, int DIR, int KIND>
 StageKernel make_stage_entry() {
   return StageKernel{L, DIR, KIND, reinterpret_cast<const void*>(&stage_kernel<L, DIR, KIND>), threads_for(L),
-                     stage_smem_bytes<L, KIND>()};
+                     stage_smem_bytes<L, KIND>(), stage_loops(L)};
 }
 
 // ----------------------------------------------------- persistent kernel
@@ -109,13 +120,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Bounded wait until *p >= target. Returns false on timeout or abort.
-__device__ __forceinline__ bool wait_counter(const unsigned int* p, unsigned int target, const PersistentArgs& a,
-                                             unsigned long long t0) {
+__device__ __forceinline__ bool wait_counter(const unsigned int* p, unsigned int target, Control* ctl,
+                                             long long timeout_ns, unsigned long long t0) {
   unsigned int spins = 0;
   while (ld_acquire(p) < target) {
     if ((++spins & 15) == 0) {
-      if (*reinterpret_cast<volatile int*>(&a.ctl->abort)) return false;
-      if ((long long)(global_ns() - t0) > a.timeout_ns) return false;
+      if (*reinterpret_cast<volatile int*>(&ctl->abort)) return false;
+      if ((long long)(global_ns() - t0) > timeout_ns) return false;
     }
     __nanosleep(100);
   }
@@ -134,10 +145,12 @@ __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDe
     complete[s - 1] = 1;
     return true;
   }
-  const long long gc = tile % d.n_gchunks;
-  const long long rest = tile / d.n_gchunks;
-  const int o = (int)(rest % d.n_outer);
-  const int b = (int)(rest / d.n_outer);
+  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
+  const unsigned t32 = (unsigned)tile;
+  const unsigned gc = t32 % (unsigned)d.n_gchunks;
+  const unsigned rest = t32 / (unsigned)d.n_gchunks;
+  const int o = (int)(rest % (unsigned)d.n_outer);
+  const int b = (int)(rest / (unsigned)d.n_outer);
   const unsigned long long t0 = global_ns();
   switch (d.dep_rule) {
     case kDepGroup: {
@@ -145,20 +158,20 @@ __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDe
       const int n16 = (d.prev_n_outer + kTileP - 1) / kTileP;
       const int outers = min(kTileP, d.prev_n_outer - (int)gc * kTileP);
       return wait_counter(a.cnt_outer16[s - 1] + (long long)b * n16 + gc,
-                          (unsigned int)(outers * d.prev_n_gchunks) + extra, a, t0);
+                          (unsigned int)(outers * d.prev_n_gchunks) + extra, a.ctl, a.timeout_ns, t0);
     }
     case kDepOuter:
       return wait_counter(a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + o,
-                          (unsigned int)d.prev_n_gchunks + extra, a, t0);
+                          (unsigned int)d.prev_n_gchunks + extra, a.ctl, a.timeout_ns, t0);
     case kDepGchunkOfOuter:
       return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + o / kTileP,
-                          (unsigned int)d.prev_n_outer + extra, a, t0);
+                          (unsigned int)d.prev_n_outer + extra, a.ctl, a.timeout_ns, t0);
     case kDepSameGchunk:
       return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + gc,
-                          (unsigned int)d.prev_n_outer + extra, a, t0);
+                          (unsigned int)d.prev_n_outer + extra, a.ctl, a.timeout_ns, t0);
     case kDepAll:
-      return wait_counter(a.cnt_total[s - 1] + b, (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra, a,
-                          t0);
+      return wait_counter(a.cnt_total[s - 1] + b, (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra, a.ctl,
+                          a.timeout_ns, t0);
   }
   return true;
 }
@@ -168,10 +181,12 @@ __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDe
 // the counter updates that consumers acquire.
 __device__ __forceinline__ void signal_done(const PersistentArgs& a, const StageDesc* st, int s, long long tile) {
   const StageDesc& d = st[s];
-  const long long gc = tile % d.n_gchunks;
-  const long long rest = tile / d.n_gchunks;
-  const int o = (int)(rest % d.n_outer);
-  const int b = (int)(rest / d.n_outer);
+  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
+  const unsigned t32 = (unsigned)tile;
+  const unsigned gc = t32 % (unsigned)d.n_gchunks;
+  const unsigned rest = t32 / (unsigned)d.n_gchunks;
+  const int o = (int)(rest % (unsigned)d.n_outer);
+  const int b = (int)(rest / (unsigned)d.n_outer);
   const int n16 = (d.n_outer + kTileP - 1) / kTileP;
   __threadfence();
   atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);

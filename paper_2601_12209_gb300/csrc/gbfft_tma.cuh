@@ -121,10 +121,12 @@ template <int L, int KIND, int SRC>
 __device__ __forceinline__ void tma_issue_tile(const CUtensorMap* map, const StageDesc& d, long long tile,
                                                float2* buf, uint64_t* bar) {
   using G = TmaGeom<L, KIND>;
-  const long long gc = tile % d.n_gchunks;
-  const long long rest = tile / d.n_gchunks;
-  const int o = (int)(rest % d.n_outer);
-  const int b = (int)(rest / d.n_outer);
+  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
+  const unsigned t32 = (unsigned)tile;
+  const unsigned gc = t32 % (unsigned)d.n_gchunks;
+  const unsigned rest = t32 / (unsigned)d.n_gchunks;
+  const int o = (int)(rest % (unsigned)d.n_outer);
+  const int b = (int)(rest / (unsigned)d.n_outer);
   const int g0 = (int)gc * kTileP;
   char* dst = reinterpret_cast<char*>(buf);
   if constexpr (SRC == kTmaRow) {
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(tma_threads(L), tma_blocks_per_sm(L))
                                                          ~static_cast<uintptr_t>(1023));
   float2* bufs = reinterpret_cast<float2*>(base);
   float2* tw = reinterpret_cast<float2*>(base + (size_t)NB * G::buf_bytes);
-  float2* tw2 = tw + tw_table_len(L);
+  constexpr int TWL = tw_table_len(L);
+  float2* tw2 = tw + TWL;
   __shared__ __align__(8) uint64_t full[NB];
   __shared__ int s_fail;
   const long long stride = gridDim.x;

@@ -1,0 +1,96 @@
+"""Batched grids: 64 C2C grids of uneven sizes (each axis drawn from
+{32,48,60,64,80,96,120,128,160,192,256}) in one launch that pulls every grid's
+tiles from one ticket queue, checked per grid against the FP64 oracle, replayed
+from a CUDA graph, and compared with one plan per grid.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_12209_gb300 import _build
+    _build.build()
+    import paper_2601_12209_gb300 as gbmod
+    return gbmod
+
+
+def test_batched_small_mixed(gb):
+    from paper_2601_12209_gb300 import abi
+    shapes = [(32, 48, 60), (60, 32, 48), (64, 64, 64), (80, 96, 32), (120, 32, 48), (48, 160, 32),
+              (192, 32, 32), (32, 32, 256)]
+    m = gb.ManyPlan(shapes)
+    grids = [synth.uniform_complex((nz, ny, nx), seed=300 + i) for i, (nx, ny, nz) in enumerate(shapes)]
+    x = m.pack([g.cuda() for g in grids])
+    y = m.empty()
+    m.exec(abi.GBFFT_OP_FORWARD, x, y)
+    z = m.empty()
+    m.exec(abi.GBFFT_OP_INVERSE, y, z)
+    torch.cuda.synchronize()
+    assert m.device_error() == 0
+    for i, (g, out, back) in enumerate(zip(grids, m.unpack(y), m.unpack(z))):
+        e = oracle.rel_l2(out.cpu().numpy(), oracle.fft3(g.numpy()))
+        e2 = oracle.rel_l2(back.cpu().numpy(), g.numpy())
+        print(f"[batched] grid {i} {shapes[i]}: fwd rel-L2 {e:.3e}, roundtrip {e2:.3e}")
+        assert e < TOL and e2 < TOL
+    # the separate-plan path gives the same bits (same tile arithmetic)
+    y2 = m.empty()
+    m.exec_separate(abi.GBFFT_OP_FORWARD, x, y2)
+    assert torch.equal(y, y2)
+
+
+def test_config4_64_uneven_grids_graph_replay(gb):
+    """Config 4: 64 grids, one persistent launch captured in a CUDA graph and replayed."""
+    from paper_2601_12209_gb300 import abi
+    shapes, grids = synth.batched_grids(64, seed=6)
+    m = gb.ManyPlan(shapes)
+    x = m.pack([g.cuda() for g in grids])
+    y = m.empty()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=s)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        m.exec(abi.GBFFT_OP_FORWARD, x, y)
+    y.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert m.device_error() == 0
+    outs = m.unpack(y)
+    rng = np.random.default_rng(0)
+    for i in sorted(rng.choice(64, size=12, replace=False).tolist()) + [0, 63]:
+        e = oracle.rel_l2(outs[i].cpu().numpy(), oracle.fft3(grids[i].numpy()))
+        print(f"[batched] cfg4 grid {i} {shapes[i]}: rel-L2 {e:.3e}")
+        assert e < TOL
+    # a second replay after the input changed in place
+    grids2 = [g.conj() for g in grids[:4]]
+    for g, off, (nx, ny, nz) in zip(grids2, m.offsets, shapes):
+        x[off:off + nx * ny * nz].copy_(g.reshape(-1).cuda())
+    graph.replay()
+    torch.cuda.synchronize()
+    for i in range(4):
+        e = oracle.rel_l2(m.unpack(y)[i].cpu().numpy(), oracle.fft3(grids2[i].numpy()))
+        assert e < TOL
+
+
+def test_batched_timeout_reported(gb):
+    from paper_2601_12209_gb300 import abi
+    m = gb.ManyPlan([(32, 32, 32), (64, 48, 32)], debug_timeout=True)
+    x = m.empty()
+    y = m.empty()
+    m.exec(abi.GBFFT_OP_FORWARD, x, y)
+    assert m.device_error() == abi.GBFFT_ERR_TIMEOUT
+    assert m.device_error() == 0
