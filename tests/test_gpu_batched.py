@@ -76,7 +76,7 @@ def test_config4_64_uneven_grids_graph_replay(gb):
         print(f"[batched] cfg4 grid {i} {shapes[i]}: rel-L2 {e:.3e}")
         assert e < TOL
     # a second replay after the input changed in place
-    grids2 = [g.conj() for g in grids[:4]]
+    grids2 = [torch.conj_physical(g) for g in grids[:4]]
     for g, off, (nx, ny, nz) in zip(grids2, m.offsets, shapes):
         x[off:off + nx * ny * nz].copy_(g.reshape(-1).cuda())
     graph.replay()
