@@ -457,9 +457,13 @@ def batched_variant(torch, gb, abi, stream, steps, warmup):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
+    graph3 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph3, stream=stream):
+        m.exec_staged(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
     res = {"grids": 64, "points": npts, "largest_smallest_ratio": max(a * b * c for a, b, c in shapes)
            / min(a * b * c for a, b, c in shapes)}
     for name, fn in (("one_launch_graph", lambda: graph.replay()),
+                     ("stage_launches_graph", lambda: graph3.replay()),
                      ("one_launch", lambda: m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)),
                      ("separate_plans", lambda: m.exec_separate(abi.GBFFT_OP_FORWARD, x, y, stream=stream))):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

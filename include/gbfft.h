@@ -256,6 +256,9 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
 int gbfft_many_layout(gbfft_many m, int grid, long long* offset, long long* total);
 /* One persistent launch for all grids; op GBFFT_OP_FORWARD or GBFFT_OP_INVERSE (1/N per grid). */
 int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* stream);
+/* The same transforms as three launches, one per stage over every grid's tiles (no
+   dependency waits; kernel boundaries order the stages); capturable as well. */
+int gbfft_many_exec_staged(gbfft_many m, int op, const void* in, void* out, void* stream);
 /* The same transforms as one plan per grid, launched one after another (for comparison). */
 int gbfft_many_exec_separate(gbfft_many m, int op, const void* in, void* out, void* stream);
 /* Read and clear the device error word of the batched launches (synchronises). */

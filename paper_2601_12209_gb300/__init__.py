@@ -203,6 +203,11 @@ class ManyPlan:
         abi.gbfft_many_exec(self.handle, int(op), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
+    def exec_staged(self, op: int, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """Three launches, one per stage over all grids (no dependency waits)."""
+        abi.gbfft_many_exec_staged(self.handle, int(op), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
     def exec_separate(self, op: int, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         abi.gbfft_many_exec_separate(self.handle, int(op), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out

@@ -49,7 +49,7 @@ EXPORTED = (
     "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version", "gbfft_exec_c2c_noalloc",
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
     "gbfft_plan_set_tuning", "gbfft_many_create", "gbfft_many_layout", "gbfft_many_exec",
-    "gbfft_many_exec_separate", "gbfft_many_get_device_error", "gbfft_many_destroy",
+    "gbfft_many_exec_separate", "gbfft_many_get_device_error", "gbfft_many_destroy", "gbfft_many_exec_staged",
 )
 
 _lib = None
@@ -104,6 +104,7 @@ def load() -> ctypes.CDLL:
             "gbfft_many_layout": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
             "gbfft_many_exec": (i, [vp, i, vp, vp, vp]),
             "gbfft_many_exec_separate": (i, [vp, i, vp, vp, vp]),
+            "gbfft_many_exec_staged": (i, [vp, i, vp, vp, vp]),
             "gbfft_many_get_device_error": (i, [vp, ctypes.POINTER(i)]),
             "gbfft_many_destroy": (None, [vp]),
             "gbfft_plan_stage_times": (i, [vp, i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i),
@@ -274,6 +275,11 @@ def gbfft_many_layout(m: int, grid: int) -> tuple[int, int]:
 
 def gbfft_many_exec(m: int, op: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
     _call("gbfft_many_exec", ctypes.c_void_p(m), int(op), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
+          ctypes.c_void_p(stream))
+
+
+def gbfft_many_exec_staged(m: int, op: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _call("gbfft_many_exec_staged", ctypes.c_void_p(m), int(op), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
           ctypes.c_void_p(stream))
 
 

@@ -1271,6 +1271,7 @@ struct gbfft_many_s {
   long long total = 0;            // complex elements of all grids
   ManySegment* segs[2] = {nullptr, nullptr};  // forward, inverse
   unsigned int* first[2] = {nullptr, nullptr};
+  std::vector<unsigned int> first_host[2];
   unsigned int tiles[2] = {0, 0};
   int nseg = 0;
   const ManyKernel* kern[2] = {nullptr, nullptr};
@@ -1380,6 +1381,7 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
           codes[pipe].push_back(code);
       }
     first[pipe].push_back(acc);
+    m->first_host[pipe] = first[pipe];
     m->tiles[pipe] = acc;
     m->kern[pipe] = find_many(codes[pipe]);
     if (!m->kern[pipe]) {
@@ -1421,7 +1423,9 @@ int gbfft_many_layout(gbfft_many m, int grid, long long* offset, long long* tota
   return GBFFT_OK;
 }
 
-int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* stream) {
+}  // extern "C"
+
+static int many_launch(gbfft_many m, int op, const void* in, void* out, void* stream, bool queue) {
   if (!m || (op != GBFFT_OP_FORWARD && op != GBFFT_OP_INVERSE)) return GBFFT_ERR_INVALID_ARG;
   int rc = check_ptrs(in, out);
   if (rc) return rc;
@@ -1442,18 +1446,42 @@ int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* strea
   const bool dbg = (m->flags & GBFFT_DEBUG_TIMEOUT) != 0;
   a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
   a.debug_never = dbg ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(&m->ctl->ticket, 0,
-                                  2 * sizeof(unsigned int) + m->counter_words * sizeof(unsigned int), st);
-  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
   const ManyKernel* k = m->kern[pipe];
   int bpsm = 1;
-  e = launch_info(k->fn, kManyThreads, k->smem, &bpsm);
+  cudaError_t e = launch_info(k->fn, kManyThreads, k->smem, &bpsm);
   if (e != cudaSuccess) return GBFFT_ERR_CUDA;
-  (void)bpsm;
-  // one block per ticket (tile); blocks start in ticket order
-  void* args[] = {&a};
-  e = cudaLaunchKernel(k->fn, dim3((unsigned)std::max<unsigned>(a.total, 1u)), dim3(kManyThreads), args, k->smem, st);
-  return cuda_err(e);
+  a.queue = queue ? 1 : 0;
+  if (queue) {
+    e = cudaMemsetAsync(&m->ctl->ticket, 0, 2 * sizeof(unsigned int) + m->counter_words * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+    // one block per ticket (tile); every block a block waits for has started
+    void* args[] = {&a};
+    e = cudaLaunchKernel(k->fn, dim3((unsigned)std::max<unsigned>(a.total, 1u)), dim3(kManyThreads), args, k->smem,
+                         st);
+    return cuda_err(e);
+  }
+  // one launch per stage over every grid's tiles of that stage
+  for (int stg = 0; stg < 3; ++stg) {
+    const unsigned lo = m->first_host[pipe][(size_t)stg * m->count];
+    const unsigned hi = m->first_host[pipe][(size_t)(stg + 1) * m->count];
+    if (hi <= lo) continue;
+    a.ticket_base = lo;
+    a.total = hi;
+    void* args[] = {&a};
+    e = cudaLaunchKernel(k->fn, dim3(hi - lo), dim3(kManyThreads), args, k->smem, st);
+    if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  }
+  return GBFFT_OK;
+}
+
+extern "C" {
+
+int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* stream) {
+  return many_launch(m, op, in, out, stream, true);
+}
+
+int gbfft_many_exec_staged(gbfft_many m, int op, const void* in, void* out, void* stream) {
+  return many_launch(m, op, in, out, stream, false);
 }
 
 int gbfft_many_exec_separate(gbfft_many m, int op, const void* in, void* out, void* stream) {

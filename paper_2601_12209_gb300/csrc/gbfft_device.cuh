@@ -269,16 +269,6 @@ __device__ __forceinline__ void dft(float2* a) {
   else if constexpr (R == 16) dft16<DIR>(a);
 }
 
-// Thread index read through a volatile instruction: the per-tile functions
-// use it instead of threadIdx.x so the compiler cannot hoist their
-// tile-invariant shared-memory addresses out of the tile loop of a kernel
-// (for mixed-radix lengths that hoisting exhausts the registers).
-__device__ __forceinline__ int tid_x() {
-  int t;
-  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t) : : "memory");
-  return t;
-}
-
 // ------------------------------------------------------------ memory helpers
 
 // Tile layout in shared memory: element n of pencil p at n*16 + swizzled p.
@@ -304,7 +294,7 @@ struct TileIO {
 // along n (coalesced), each lane moves one pencil pair as a 16-byte smem chunk.
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_load(float2* sm, const TileIO& io) {
-  for (int it = tid_x(); it < NROWS * 8; it += THREADS) {
+  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
@@ -318,7 +308,7 @@ template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
   const float sc = io.scale;
   const bool unit = sc == 1.f;
-  for (int it = tid_x(); it < NROWS * 8; it += THREADS) {
+  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float4 v = *reinterpret_cast<const float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1)));
@@ -332,7 +322,7 @@ __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
 // along p, so 16 lanes move one 128-byte line.
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
-  for (int it = tid_x(); it < NROWS * 16; it += THREADS) {
+  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
     int p = it & 15, n = it >> 4;
     float2 a = make_float2(0.f, 0.f);
     if (p < io.valid) a = ld_data(io.gin + p + n * io.in_n);
@@ -342,7 +332,7 @@ __device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
 
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void col_store(const float2* sm, const TileIO& io) {
-  for (int it = tid_x(); it < NROWS * 16; it += THREADS) {
+  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
     int p = it & 15, n = it >> 4;
     if (p < io.valid) {
       float2 v = sm[swz(n, p)];
@@ -389,7 +379,7 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
   constexpr int G = THREADS / 16;
   constexpr int NBT = (NB + G - 1) / G;
   constexpr int TWO = tw_pass_offset(L, PASS);  // evaluated at compile time
-  const int p = tid_x() & 15, g = tid_x() >> 4;
+  const int p = threadIdx.x & 15, g = threadIdx.x >> 4;
   float2 v[NBT][R];
   static_for<NBT>([&](auto tc) {
     constexpr int t = decltype(tc)::value;
@@ -495,7 +485,7 @@ __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const T
 template <int M, int THREADS>
 __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float interior) {
   constexpr int NPAIR = M / 2 + 1;
-  for (int it = tid_x(); it < NPAIR * 16; it += THREADS) {
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
     const int p = it & 15, k = it >> 4;
     if (k == 0) {
       float2 z0 = sm[swz(0, p)];
@@ -525,7 +515,7 @@ __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float in
 template <int M, int THREADS>
 __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float interior) {
   constexpr int NPAIR = M / 2 + 1;
-  for (int it = tid_x(); it < NPAIR * 16; it += THREADS) {
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
     const int p = it & 15, k = it >> 4;
     if (k == 0) {
       float a = sm[swz(0, p)].x, c = sm[swz(M, p)].x;
@@ -551,7 +541,7 @@ __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float int
 template <int L, int THREADS>
 __device__ __forceinline__ void poisson_multiply(float2* sm, int gfirst, int ky_idx, int ny, float inv_n) {
   const float ky = (float)(ky_idx <= ny / 2 ? ky_idx : ky_idx - ny);
-  for (int it = tid_x(); it < L * 16; it += THREADS) {
+  for (int it = threadIdx.x; it < L * 16; it += THREADS) {
     const int p = it & 15, n = it >> 4;
     const float kx = (float)(gfirst + p);
     const float kz = (float)(n <= L / 2 ? n : n - L);
@@ -673,9 +663,9 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
 template <int L, int THREADS>
 __device__ __forceinline__ void load_twiddles(float2* tw_s, float2* tw2_s, const StageDesc& d, bool need_tw2) {
   constexpr int TWL = tw_table_len(L);
-  for (int i = tid_x(); i < TWL; i += THREADS) tw_s[i] = d.tw[i];
+  for (int i = threadIdx.x; i < TWL; i += THREADS) tw_s[i] = d.tw[i];
   if (need_tw2)
-    for (int i = tid_x(); i <= L; i += THREADS) tw2_s[i] = d.tw2[i];
+    for (int i = threadIdx.x; i <= L; i += THREADS) tw2_s[i] = d.tw2[i];
 }
 
 }  // namespace gbfft

@@ -42,6 +42,11 @@ struct ManyArgs {
   unsigned int* counters;
   long long timeout_ns;
   int debug_never;
+  // queue = 1: blocks take tickets from ctl->ticket and wait on dependencies
+  // (all stages in one launch); queue = 0: block b runs ticket ticket_base + b
+  // with no waits (one launch per stage, kernel boundaries order the stages)
+  int queue;
+  unsigned int ticket_base;
 };
 
 constexpr int kManyThreads = 256;
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(kManyThreads, 2) many_kernel(ManyArgs a) {
   __shared__ long long s_tile;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    const unsigned int t = a.queue ? atomicAdd(&a.ctl->ticket, 1u) : a.ticket_base + blockIdx.x;
     int ok = t < a.total ? 1 : 0;
     if (ok) {
       // segment of ticket t: the last s with first[s] <= t
@@ -137,8 +142,8 @@ __global__ void __launch_bounds__(kManyThreads, 2) many_kernel(ManyArgs a) {
       s_seg.d.in = bases_in[s_seg.in_buf] + s_seg.in_off;
       s_seg.d.out = bases_out[s_seg.out_buf] + s_seg.out_off;
       s_tile = (long long)(t - a.first[lo]);
-      if (*reinterpret_cast<volatile int*>(&a.ctl->abort)) ok = 0;
-      if (ok && !many_wait(a, s_seg, s_tile)) {
+      if (a.queue && *reinterpret_cast<volatile int*>(&a.ctl->abort)) ok = 0;
+      if (a.queue && ok && !many_wait(a, s_seg, s_tile)) {
         atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
         atomicExch(&a.ctl->abort, 1);
         ok = 0;
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(kManyThreads, 2) many_kernel(ManyArgs a) {
   __syncthreads();
   dispatch_tile<kManyThreads, CODES...>(stage_code(s_seg.d), s_seg.d, s_tile, sm, tw, tw);
   __syncthreads();
-  if (threadIdx.x == 0) many_signal(a, s_seg, s_tile);
+  if (a.queue && threadIdx.x == 0) many_signal(a, s_seg, s_tile);
 }
 
 struct ManyKernel {

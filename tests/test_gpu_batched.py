@@ -43,10 +43,16 @@ def test_batched_small_mixed(gb):
         e2 = oracle.rel_l2(back.cpu().numpy(), g.numpy())
         print(f"[batched] grid {i} {shapes[i]}: fwd rel-L2 {e:.3e}, roundtrip {e2:.3e}")
         assert e < TOL and e2 < TOL
-    # the separate-plan path gives the same bits (same tile arithmetic)
+    # the per-stage launches and the one-plan-per-grid path give the same bits (same tile arithmetic)
     y2 = m.empty()
     m.exec_separate(abi.GBFFT_OP_FORWARD, x, y2)
     assert torch.equal(y, y2)
+    y3 = m.empty()
+    m.exec_staged(abi.GBFFT_OP_FORWARD, x, y3)
+    assert torch.equal(y, y3)
+    z3 = m.empty()
+    m.exec_staged(abi.GBFFT_OP_INVERSE, y3, z3)
+    assert torch.equal(z, z3)
 
 
 def test_config4_64_uneven_grids_graph_replay(gb):
