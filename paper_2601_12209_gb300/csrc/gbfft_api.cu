@@ -1271,6 +1271,7 @@ struct gbfft_many_s {
   long long total = 0;            // complex elements of all grids
   ManySegment* segs[2] = {nullptr, nullptr};  // forward, inverse
   unsigned int* first[2] = {nullptr, nullptr};
+  unsigned char* tile_seg[2] = {nullptr, nullptr};
   std::vector<unsigned int> first_host[2];
   unsigned int tiles[2] = {0, 0};
   int nseg = 0;
@@ -1287,6 +1288,7 @@ static void free_many(gbfft_many_s* m) {
   for (int i = 0; i < 2; ++i) {
     cudaFree(m->segs[i]);
     cudaFree(m->first[i]);
+    cudaFree(m->tile_seg[i]);
   }
   cudaFree(m->ws);
   cudaFree(m->ctl);
@@ -1399,6 +1401,13 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
          cudaMalloc(&m->first[pipe], first[pipe].size() * sizeof(unsigned int)) == cudaSuccess &&
          cudaMemcpy(m->first[pipe], first[pipe].data(), first[pipe].size() * sizeof(unsigned int),
                     cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+      std::vector<unsigned char> ts(m->tiles[pipe]);
+      for (size_t sg = 0; sg + 1 < first[pipe].size(); ++sg)
+        for (unsigned t = first[pipe][sg]; t < first[pipe][sg + 1]; ++t) ts[t] = (unsigned char)sg;
+      ok = cudaMalloc(&m->tile_seg[pipe], std::max<size_t>(ts.size(), 1)) == cudaSuccess &&
+           cudaMemcpy(m->tile_seg[pipe], ts.data(), ts.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
   }
   void* c = nullptr;
   ok = ok && cudaMalloc(&m->ws, (size_t)m->total * sizeof(float2)) == cudaSuccess &&
@@ -1436,6 +1445,7 @@ static int many_launch(gbfft_many m, int op, const void* in, void* out, void* st
   std::memset(&a, 0, sizeof(a));
   a.segs = m->segs[pipe];
   a.first = m->first[pipe];
+  a.tile_seg = m->tile_seg[pipe];
   a.nseg = m->nseg;
   a.total = m->tiles[pipe];
   a.in = reinterpret_cast<const float2*>(in);

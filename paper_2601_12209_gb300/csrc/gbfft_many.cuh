@@ -33,6 +33,7 @@ struct ManySegment {
 struct ManyArgs {
   const ManySegment* segs;
   const unsigned int* first;  // nseg + 1 prefix sums of tiles
+  const unsigned char* tile_seg;  // segment of every ticket
   int nseg;
   unsigned int total;
   const float2* in;
@@ -117,39 +118,41 @@ __device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment
 // straight-line tile per block also keeps the eleven lengths' butterflies in
 // registers (inside a tile loop the compiler spills them).
 template <int... CODES>
-__global__ void __launch_bounds__(kManyThreads, 2) many_kernel(ManyArgs a) {
+__global__ void __launch_bounds__(kManyThreads, 3) many_kernel(ManyArgs a) {
   constexpr int LM = many_max_len<CODES...>();
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* tw = sm + (LM + 1) * kTileP;  // 16-byte aligned: (LM + 1) * 16 float2
-  __shared__ ManySegment s_seg;
+  __shared__ __align__(16) ManySegment s_seg;
   __shared__ long long s_tile;
+  __shared__ unsigned int s_t;
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     const unsigned int t = a.queue ? atomicAdd(&a.ctl->ticket, 1u) : a.ticket_base + blockIdx.x;
-    int ok = t < a.total ? 1 : 0;
-    if (ok) {
-      // segment of ticket t: the last s with first[s] <= t
-      int lo = 0, hi = a.nseg - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.first[mid] <= t) lo = mid;
-        else hi = mid - 1;
-      }
-      s_seg = a.segs[lo];
+    s_t = t;
+    s_ok = (t < a.total && !(a.queue && *reinterpret_cast<volatile int*>(&a.ctl->abort))) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const unsigned int t = s_t;
+  const int seg = a.tile_seg[t];
+  if (threadIdx.x < 32) {  // warp 0 copies the segment descriptor, 8 bytes per lane
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(a.segs + seg);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_seg);
+    for (int i = threadIdx.x; i < (int)(sizeof(ManySegment) / 8); i += 32) dst[i] = src[i];
+    __syncwarp();
+    if (threadIdx.x == 0) {
       const float2* bases_in[3] = {a.in, a.out, a.ws};
       float2* bases_out[3] = {const_cast<float2*>(a.in), a.out, a.ws};
       s_seg.d.in = bases_in[s_seg.in_buf] + s_seg.in_off;
       s_seg.d.out = bases_out[s_seg.out_buf] + s_seg.out_off;
-      s_tile = (long long)(t - a.first[lo]);
-      if (a.queue && *reinterpret_cast<volatile int*>(&a.ctl->abort)) ok = 0;
-      if (a.queue && ok && !many_wait(a, s_seg, s_tile)) {
+      s_tile = (long long)(t - a.first[seg]);
+      if (a.queue && !many_wait(a, s_seg, s_tile)) {
         atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
         atomicExch(&a.ctl->abort, 1);
-        ok = 0;
+        s_ok = 0;
       }
     }
-    s_ok = ok;
   }
   __syncthreads();
   if (!s_ok) return;
