@@ -508,6 +508,56 @@ def poisson_variant(torch, gb, abi, stream, steps, warmup):
     return out
 
 
+def precision_variant(torch, gb, abi, stream, steps, warmup):
+    """1024^3 C2C: FP32 butterflies vs tensor-core radix-16 passes with FP16 / BF16 hi/lo pairs.
+
+    Timing input: uniform[-1,1] noise drawn on the device from a seeded generator plus 16
+    plane waves (the FFT's work does not depend on the values). Accuracy without the oracle:
+    the waves alone against their closed form n^3 a_m (peak error, energy leaked elsewhere)
+    and the round trip of the full input.
+    """
+    import numpy as np
+    import synth
+    n = 1024
+    N = n ** 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    x = torch.complex(torch.rand((n, n, n), generator=g, device="cuda") * 2 - 1,
+                      torch.rand((n, n, n), generator=g, device="cuda") * 2 - 1)
+    ks, amps = synth.plane_wave_spec(n, seed=7)
+    synth.add_plane_waves(x, ks, amps)
+    waves = synth.add_plane_waves(torch.zeros_like(x), ks, amps)
+    pk = torch.as_tensor(ks, device="cuda")
+    out = {"grid": [n, n, n], "flops_5nlog2n": flops_5n(n, n, n), "alg_bytes": c2c_alg_bytes(n, n, n)}
+    for name, kw in (("fp32_tuned", {}), ("fp32_staged_lsu", {"staged": True, "tma": False}),
+                     ("fp16_split", {"precision": "fp16_split"}), ("bf16_split", {"precision": "bf16_split"})):
+        p = gb.Plan(n, n, n, **kw)
+        if name == "fp32_tuned":
+            p.autotune(stream)
+        med, _ = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+        y = p.forward(x)
+        z = p.inverse(y)
+        rt = float(torch.linalg.vector_norm((z.to(torch.complex128) - x.to(torch.complex128)).reshape(-1))
+                   / torch.linalg.vector_norm(x.to(torch.complex128).reshape(-1)))
+        del z
+        w = p.forward(waves, out=y)
+        peaks = w[pk[:, 2], pk[:, 1], pk[:, 0]].cpu().numpy().astype(np.complex128)
+        w[pk[:, 2], pk[:, 1], pk[:, 0]] = 0
+        leak = float(torch.linalg.vector_norm(w.reshape(-1).to(torch.complex128))) / float(
+            np.sqrt(np.sum(np.abs(N * amps) ** 2)))
+        torch.cuda.synchronize()
+        out[name] = {"fwd_ms": med[0], "inv_ms": med[1],
+                     "fwd_gflops": flops_5n(n, n, n) / (med[0] * 1e-3) / 1e9,
+                     "fwd_alg_gbs": c2c_alg_bytes(n, n, n) / (med[0] * 1e-3) / 1e9,
+                     "peak_rel_err": float(np.max(np.abs(peaks - N * amps) / np.abs(N * amps))),
+                     "leak_rel": leak, "round_trip_rel_l2": rt, "device_error": p.device_error()}
+        del y, w
+        p.close()
+    del x, waves
+    torch.cuda.empty_cache()
+    return out
+
+
 def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
     """C2C 512^3 pencil and slab, R2C slab, forward+adjoint: per-launch medians."""
     import synth
@@ -560,6 +610,7 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
     del x
     out["batched_64"] = batched_variant(torch, gb, abi, stream, steps, warmup)
     out["poisson_256"] = poisson_variant(torch, gb, abi, stream, steps, warmup)
+    out["precision_1024"] = precision_variant(torch, gb, abi, stream, min(steps, 10), warmup)
     # cuFFT via torch.fft on the same GPU: context only, not a target
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(warmup):

@@ -55,6 +55,15 @@ typedef struct gbfft_plan_s* gbfft_plan;
 
 /* arithmetic: storage is always float32 / complex64 */
 #define GBFFT_FP32 0
+/* Storage stays complex64 in every mode; the radix-16 passes run as dense
+ * 16x16 DFT products on the tensor cores with each FP32 operand split into a
+ * hi/lo pair of FP16 (or BF16) values, three products per term, FP32
+ * accumulation, and a power-of-two scale per butterfly. Not in the paper: an
+ * extension of its per-axis 1D FFT step (Section III-A). C2C plans only;
+ * axes whose length has no radix-16 pass (or is 16 itself, a half-warp
+ * kernel) keep the FP32 butterflies. */
+#define GBFFT_FP16_SPLIT 1
+#define GBFFT_BF16_SPLIT 2
 
 /* plan flags */
 #define GBFFT_PENCIL 0u          /* three stages, two redistributions (Algorithm 1) */
@@ -90,7 +99,8 @@ typedef struct gbfft_plan_s* gbfft_plan;
  * Create a plan for `batch` grids of nx x ny x nz (Section V-B: a reusable
  * plan keyed by data type, size, transform type and dimensions).
  *   kind  : GBFFT_C2C or GBFFT_R2C (R2C needs even nx)
- *   dtype : GBFFT_FP32
+ *   dtype : GBFFT_FP32, or GBFFT_FP16_SPLIT / GBFFT_BF16_SPLIT (kind C2C
+ *           only; stage launches without tensor copies, whatever the flags)
  *   flags : GBFFT_PENCIL or GBFFT_SLAB, optionally | GBFFT_TRANSPOSED_OUT
  *           (pencil only) | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT
  * Every axis length (nx/2 for the R2C x axis) must satisfy

@@ -49,12 +49,16 @@ class Plan:
     kind: "c2c" or "r2c"; slab: plane-wise x,y then z (else pencil);
     transposed_out: pencil forward output left as [b][kx][ky][kz];
     staged: one launch per stage instead of the persistent launch;
-    tma=False: staged launches load tiles with thread loads instead of tensor copies.
+    tma=False: staged launches load tiles with thread loads instead of tensor copies;
+    precision: "fp32", or "fp16_split" / "bf16_split" (c2c only: radix-16 passes
+    on the tensor cores with hi/lo operand pairs; storage stays complex64).
     """
+
+    _PRECISIONS = {"fp32": abi.GBFFT_FP32, "fp16_split": abi.GBFFT_FP16_SPLIT, "bf16_split": abi.GBFFT_BF16_SPLIT}
 
     def __init__(self, nx: int, ny: int, nz: int, kind: str = "c2c", batch: int = 1, slab: bool = False,
                  transposed_out: bool = False, staged: bool = False, debug_timeout: bool = False,
-                 cached: bool = False, tma: bool = True):
+                 cached: bool = False, tma: bool = True, precision: str = "fp32"):
         self.nx, self.ny, self.nz, self.batch = int(nx), int(ny), int(nz), int(batch)
         self.kind = kind
         k = GBFFT_R2C if kind == "r2c" else GBFFT_C2C
@@ -67,7 +71,10 @@ class Plan:
         self.transposed_out = transposed_out
         self._cached = cached
         mk = abi.gbfft_plan_get_cached if cached else abi.gbfft_plan_create
-        self.handle = mk(self.nx, self.ny, self.nz, k, abi.GBFFT_FP32, self.batch, flags)
+        if precision not in self._PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(self._PRECISIONS)}")
+        self.precision = precision
+        self.handle = mk(self.nx, self.ny, self.nz, k, self._PRECISIONS[precision], self.batch, flags)
         self.nxc = self.nx // 2 + 1 if kind == "r2c" else self.nx
         self._ws = None
 

@@ -27,6 +27,10 @@ void register_stage_group_4(std::vector<StageKernel>&);
 void register_stage_group_5(std::vector<StageKernel>&);
 void register_stage_group_6(std::vector<StageKernel>&);
 void register_stage_group_7(std::vector<StageKernel>&);
+void register_split_group_0(std::vector<StageKernel>&);
+void register_split_group_1(std::vector<StageKernel>&);
+void register_split_group_2(std::vector<StageKernel>&);
+void register_split_group_3(std::vector<StageKernel>&);
 void register_persistent_group_0(std::vector<PersistentKernel>&);
 void register_persistent_group_1(std::vector<PersistentKernel>&);
 void register_tma_group_0(std::vector<TmaKernel>&);
@@ -58,6 +62,10 @@ static void ensure_registry() {
     register_stage_group_5(s);
     register_stage_group_6(s);
     register_stage_group_7(s);
+    register_split_group_0(s);
+    register_split_group_1(s);
+    register_split_group_2(s);
+    register_split_group_3(s);
     auto& p = persistent_registry();
     register_persistent_group_0(p);
     register_persistent_group_1(p);
@@ -96,10 +104,22 @@ static int host_radices(int n, int* out, int cap) {
   return cnt;
 }
 
-static const StageKernel* find_stage(int L, int dir, int kind) {
+// Lengths with tensor-core passes: a radix-16 pass and whole warps (length 16
+// alone runs as a 16-thread block and keeps the FP32 butterflies).
+static bool split_capable(int L) {
+  const Radices R = make_radices(L);
+  bool r16 = false;
+  for (int i = 0; i < R.n; ++i) r16 |= R.r[i] == 16;
+  return r16 && threads_for(L) % 32 == 0;
+}
+
+// Lengths without tensor-core passes run the same FP32 arithmetic in every
+// precision mode, so a split-precision request takes the FP32 kernel.
+static const StageKernel* find_stage(int L, int dir, int kind, int prec = kPrecFP32) {
   ensure_registry();
+  if (prec != kPrecFP32 && !split_capable(L)) prec = kPrecFP32;
   for (const auto& k : stage_registry())
-    if (k.L == L && k.dir == dir && k.kind == kind) return &k;
+    if (k.L == L && k.dir == dir && k.kind == kind && k.prec == prec) return &k;
   return nullptr;
 }
 
@@ -479,6 +499,8 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       add(Xi, 2, 1);
     }
   }
+  for (int s = 0; s < P.n; ++s)
+    if (P.st[s].kind == kPlain) P.st[s].prec = p->dtype;  // GBFFT_*_SPLIT values equal the StagePrec values
   return P;
 }
 
@@ -503,6 +525,8 @@ static size_t counter_words(const Pipeline& P) {
 
 static const PersistentKernel* find_persistent(const Pipeline& P) {
   ensure_registry();
+  for (int s = 0; s < P.n; ++s)
+    if (P.st[s].prec != kPrecFP32) return nullptr;  // tensor-core passes run in stage launches only
   for (const auto& k : persistent_registry()) {
     bool all = true;
     for (int s = 0; s < P.n && all; ++s) {
@@ -520,7 +544,7 @@ static const PersistentKernel* find_persistent(const Pipeline& P) {
 // layout can be described by a tensor map, else the load/store kernel.
 static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags = 0, int* err = nullptr) {
   if (d.n_tiles == 0) return GBFFT_OK;
-  if (!(flags & GBFFT_NO_TMA) && err && d.kind != kIdentity) {
+  if (!(flags & GBFFT_NO_TMA) && err && d.kind != kIdentity && d.prec == kPrecFP32) {
     const int src = d.in_mode == kRow ? 1 : 2;
     const TmaKernel* tk = find_tma(d.L, d.dir, d.kind, src);
     alignas(64) CUtensorMap map;
@@ -536,7 +560,7 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags 
       return cuda_err(e);
     }
   }
-  const StageKernel* k = find_stage(d.L, d.dir, d.kind);
+  const StageKernel* k = find_stage(d.L, d.dir, d.kind, d.prec);
   if (!k) return GBFFT_ERR_UNSUPPORTED_SIZE;
   int bpsm = 1;
   cudaError_t e = launch_info(k->fn, k->threads, k->smem, &bpsm);
@@ -816,13 +840,18 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   *out = nullptr;
   if (nx < 2 || ny < 2 || nz < 2 || batch < 1) return GBFFT_ERR_INVALID_ARG;
   if (kind != GBFFT_C2C && kind != GBFFT_R2C) return GBFFT_ERR_INVALID_ARG;
-  if (dtype != GBFFT_FP32) return GBFFT_ERR_INVALID_ARG;
+  if (dtype != GBFFT_FP32 && dtype != GBFFT_FP16_SPLIT && dtype != GBFFT_BF16_SPLIT) return GBFFT_ERR_INVALID_ARG;
+  // split precision: complex transforms only (the real-data and Poisson kinds keep FP32)
+  if (dtype != GBFFT_FP32 && kind != GBFFT_C2C) return GBFFT_ERR_INVALID_ARG;
   const unsigned known = GBFFT_SLAB | GBFFT_TRANSPOSED_OUT | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT;
   if (flags & ~known) return GBFFT_ERR_INVALID_ARG;
   if ((flags & GBFFT_SLAB) && (flags & GBFFT_TRANSPOSED_OUT)) return GBFFT_ERR_INVALID_ARG;
   if (kind == GBFFT_R2C && (nx % 2 != 0 || nx < 4)) return GBFFT_ERR_INVALID_ARG;
   const int Lx = kind == GBFFT_R2C ? nx / 2 : nx;
   if (!stage_supported(Lx) || !stage_supported(ny) || !stage_supported(nz)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  for (int L : {nx, ny, nz})
+    if (dtype != GBFFT_FP32 && (!find_stage(L, -1, kPlain, dtype) || !find_stage(L, 1, kPlain, dtype)))
+      return GBFFT_ERR_UNSUPPORTED_SIZE;
   if (kind == GBFFT_R2C && (!find_stage(Lx, -1, kR2CPost) || !find_stage(Lx, 1, kC2RPre)))
     return GBFFT_ERR_UNSUPPORTED_SIZE;
   int ndev = 0;
@@ -1046,7 +1075,7 @@ int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* 
 // Whether stage d can run with the tensor-copy kernel (one exists for its
 // length/kind/side and its input layout has a tensor map).
 static bool tma_possible(const StageDesc& d) {
-  if (d.kind == kIdentity) return false;
+  if (d.kind == kIdentity || d.prec != kPrecFP32) return false;
   const int src = d.in_mode == kRow ? 1 : 2;
   if (!find_tma(d.L, d.dir, d.kind, src)) return false;
   alignas(64) CUtensorMap m;
@@ -1381,6 +1410,13 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
         const int code = kcode(s.d.L, s.d.kind, s.d.dir);
         if (std::find(codes[pipe].begin(), codes[pipe].end(), code) == codes[pipe].end())
           codes[pipe].push_back(code);
+      }
+    // each segment publishes only the counters its consumer (next stage, same grid) waits on
+    for (int k = 0; k + 1 < 3; ++k)
+      for (int g = 0; g < count; ++g) {
+        ManySegment& s = segs[pipe][(size_t)k * count + g];
+        const int rule = segs[pipe][(size_t)(k + 1) * count + g].d.dep_rule;
+        s.sig_mask = kSigStage | (rule == kDepGroup ? kSigOuter16 : 0) | (rule == kDepGchunkOfOuter ? kSigGchunk : 0);
       }
     first[pipe].push_back(acc);
     m->first_host[pipe] = first[pipe];

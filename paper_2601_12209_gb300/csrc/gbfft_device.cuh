@@ -16,6 +16,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <utility>
 
 #include "gbfft_internal.h"
@@ -457,12 +460,209 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
   }
 }
 
+// ------------------------------------ split-precision tensor-core radix 16
+//
+// A radix-16 Stockham pass applies the 16-point DFT matrix
+// F[q][r] = exp(s 2 pi i q r / 16) (s = -1 forward, +1 inverse) to the
+// twiddled inputs of every butterfly: with one column per butterfly (pencil
+// p, group j), the pass is the dense product Y = F X, in real form
+// Yr = Fr Xr - Fi Xi and Yi = Fi Xr + Fr Xi. Here it runs on the tensor cores
+// (mma.sync m16n8k16, FP32 accumulation): each real operand a is split into a
+// pair of 16-bit floats hi = rn(a), lo = rn(a - hi), and each product keeps
+// the three terms hi.hi + hi.lo + lo.hi (the dropped lo.lo term is about
+// 2^-22 of the operand scale with FP16, 2^-16 with BF16). Before the split,
+// each column is scaled by the power of two that puts its largest component
+// in [0.5, 1) (inside the FP16 range); the outputs are scaled back exactly.
+// Twiddles and the data exchange stay in FP32, as in the FP32 pass.
+
+// cos(2 pi m / 16) for m in [0, 16), from the constants of the FP32 radix 16
+__device__ __forceinline__ float cos16(int m) {
+  const int a = m & 7;  // cos(x + pi) = -cos x
+  const int b = a <= 4 ? a : 8 - a;  // cos(pi - x) = -cos x
+  float v = b == 0 ? 1.f : b == 1 ? kC16_1 : b == 2 ? kSqrtHalf : b == 3 ? kS16_1 : 0.f;
+  if (a > 4) v = -v;
+  return (m & 8) ? -v : v;
+}
+
+// hi/lo pairs of (a, b), packed low element first as mma operands expect
+template <int PREC>
+__device__ __forceinline__ void split16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  if constexpr (PREC == kPrecF16Split) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+
+// D += A B for one m16n8k16 tile: A 16x16 row-major fragment, B 16x8 fragment
+template <int PREC>
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  if constexpr (PREC == kPrecF16Split) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  } else {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  }
+}
+
+// This lane's A fragments of Fr and Fi (hi and lo). Fragment register i holds
+// rows q = g + 8 (i & 1), columns r = 2t + 8 (i >> 1) + {0, 1}, with
+// g = lane / 4, t = lane % 4 (the m16n8k16 operand layout).
+template <int PREC, int DIR>
+struct Dft16Frags {
+  uint32_t re_hi[4], re_lo[4], im_hi[4], im_lo[4];
+  __device__ __forceinline__ Dft16Frags() {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float sg = DIR < 0 ? -1.f : 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = g + ((i & 1) << 3);
+      const int r = 2 * t + ((i >> 1) << 3);
+      const int m0 = (q * r) & 15, m1 = (q * (r + 1)) & 15;
+      split16x2<PREC>(cos16(m0), cos16(m1), re_hi[i], re_lo[i]);
+      // sin(2 pi m / 16) = cos(2 pi (m - 4) / 16)
+      split16x2<PREC>(sg * cos16((m0 + 12) & 15), sg * cos16((m1 + 12) & 15), im_hi[i], im_lo[i]);
+    }
+  }
+};
+
+// The radix-16 pass PASS of a length-L tile on the tensor cores. A column
+// group is 8 butterflies of one group j (pencils 8h..8h+7, h = cg & 1); lane
+// (g, t) loads inputs r = 2t, 2t+1, 2t+8, 2t+9 of butterfly (j, 8h+g) -- the
+// m16n8k16 B layout -- and receives outputs q = g, g+8 of butterflies
+// (j, 8h+2t) and (j, 8h+2t+1). Reads, barrier, writes as in stockham_pass.
+template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, bool SYNC_BEFORE_WRITE, int PREC>
+__device__ __forceinline__ void stockham_pass_tc16(float2* sm, const float2* tw, const TileIO& io) {
+  constexpr int R = 16;
+  static_assert(make_radices(L).r[PASS] == R, "tensor-core pass is radix 16");
+  static_assert(kTileP == 16 && THREADS % 32 == 0, "two column groups of 8 pencils per tile row");
+  constexpr int Ns = radix_prefix(L, PASS);
+  constexpr int NB = L / R;
+  constexpr int CG = NB * 2;
+  constexpr int W = THREADS / 32;
+  constexpr int CGT = (CG + W - 1) / W;
+  constexpr int TWO = tw_pass_offset(L, PASS);
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  const Dft16Frags<PREC, DIR> F;
+  float acc[CGT][8];
+  static_for<CGT>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const int cg = warp + i * W;
+    if (CG % W == 0 || cg < CG) {
+      const int j = cg >> 1;
+      const int p = ((cg & 1) << 3) + gq;
+      float2 x[4];
+      static_for<4>([&](auto uc) {
+        constexpr int u = decltype(uc)::value;
+        const int n = j + (2 * tq + (u & 1) + ((u >> 1) << 3)) * NB;
+        if constexpr (SRC_GLOBAL) {
+          x[u] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
+        } else {
+          x[u] = sm[swz(n, p)];
+        }
+      });
+      if constexpr (Ns > 1) {
+        // tw is 16-byte aligned and TWO + k R + 2t is even
+        const float2* twp = tw + TWO + (j % Ns) * R + 2 * tq;
+        const float4 w0 = *reinterpret_cast<const float4*>(twp);
+        const float4 w1 = *reinterpret_cast<const float4*>(twp + 8);
+        x[0] = cmul(x[0], tw_dir<DIR>(make_float2(w0.x, w0.y)));
+        x[1] = cmul(x[1], tw_dir<DIR>(make_float2(w0.z, w0.w)));
+        x[2] = cmul(x[2], tw_dir<DIR>(make_float2(w1.x, w1.y)));
+        x[3] = cmul(x[3], tw_dir<DIR>(make_float2(w1.z, w1.w)));
+      }
+      // power-of-two column scale: the 4 lanes of a column reduce their maxima
+      float m = fmaxf(fmaxf(fmaxf(fabsf(x[0].x), fabsf(x[0].y)), fmaxf(fabsf(x[1].x), fabsf(x[1].y))),
+                      fmaxf(fmaxf(fabsf(x[2].x), fabsf(x[2].y)), fmaxf(fabsf(x[3].x), fabsf(x[3].y))));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
+      m = fmaxf(m, __shfl_xor_sync(kFull, m, 2));
+      int e = (int)((__float_as_uint(m) >> 23) & 0xffu);  // m in [2^(e-127), 2^(e-126))
+      e = e == 0 ? 126 : min(e, 252);                      // zero or subnormal column: scale 1
+      const float sc = __uint_as_float((uint32_t)(253 - e) << 23);  // 2^(126 - e)
+      uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
+      split16x2<PREC>(x[0].x * sc, x[1].x * sc, rh0, rl0);
+      split16x2<PREC>(x[2].x * sc, x[3].x * sc, rh1, rl1);
+      split16x2<PREC>(x[0].y * sc, x[1].y * sc, ih0, il0);
+      split16x2<PREC>(x[2].y * sc, x[3].y * sc, ih1, il1);
+      constexpr uint32_t kNeg = 0x80008000u;  // sign bits of both 16-bit halves
+      float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
+      // small terms first, then hi.hi
+      mma_16816<PREC>(yr, F.re_hi, rl0, rl1);
+      mma_16816<PREC>(yr, F.re_lo, rh0, rh1);
+      mma_16816<PREC>(yr, F.im_hi, il0 ^ kNeg, il1 ^ kNeg);
+      mma_16816<PREC>(yr, F.im_lo, ih0 ^ kNeg, ih1 ^ kNeg);
+      mma_16816<PREC>(yr, F.re_hi, rh0, rh1);
+      mma_16816<PREC>(yr, F.im_hi, ih0 ^ kNeg, ih1 ^ kNeg);
+      mma_16816<PREC>(yi, F.im_hi, rl0, rl1);
+      mma_16816<PREC>(yi, F.im_lo, rh0, rh1);
+      mma_16816<PREC>(yi, F.re_hi, il0, il1);
+      mma_16816<PREC>(yi, F.re_lo, ih0, ih1);
+      mma_16816<PREC>(yi, F.im_hi, rh0, rh1);
+      mma_16816<PREC>(yi, F.re_hi, ih0, ih1);
+      // output columns 2t and 2t+1 were scaled by the lanes 8t and 8t+4
+      const int e0 = __shfl_sync(kFull, e, 8 * tq);
+      const int e1 = __shfl_sync(kFull, e, 8 * tq + 4);
+      const float s0 = __uint_as_float((uint32_t)(e0 + 1) << 23);  // 2^(e0 - 126)
+      const float s1 = __uint_as_float((uint32_t)(e1 + 1) << 23);
+      acc[i][0] = yr[0] * s0;  // q = g, pencil 8h + 2t
+      acc[i][1] = yi[0] * s0;
+      acc[i][2] = yr[1] * s1;  // q = g, pencil 8h + 2t + 1
+      acc[i][3] = yi[1] * s1;
+      acc[i][4] = yr[2] * s0;  // q = g + 8
+      acc[i][5] = yi[2] * s0;
+      acc[i][6] = yr[3] * s1;
+      acc[i][7] = yi[3] * s1;
+    }
+  });
+  if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
+  static_for<CGT>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const int cg = warp + i * W;
+    if (CG % W == 0 || cg < CG) {
+      const int j = cg >> 1;
+      const int pc = ((cg & 1) << 3) + 2 * tq;
+      if constexpr (DST_GLOBAL) {
+        // last pass (Ns R = L): output q of group j is element j + q NB
+        const float f = io.scale;
+        static_for<4>([&](auto vc) {
+          constexpr int v = decltype(vc)::value;
+          const int pp = pc + (v & 1);
+          const int n = j + (gq + ((v >> 1) << 3)) * NB;
+          if (pp < io.valid) st_data(io.gout + pp + n * io.out_n, make_float2(acc[i][2 * v] * f, acc[i][2 * v + 1] * f));
+        });
+      } else {
+        const int k = j % Ns;
+        const int base = (j - k) * R + k;
+        // pencils pc, pc + 1 stay adjacent under the swizzle (pc even)
+        *reinterpret_cast<float4*>(sm + swz(base + gq * Ns, pc)) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(sm + swz(base + (gq + 8) * Ns, pc)) =
+            make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      }
+    }
+  });
+  if constexpr (!DST_GLOBAL) __syncthreads();
+}
+
 // All passes of a length-L transform. The data starts in shared memory unless
 // SRC_GLOBAL, and ends in shared memory unless DST_GLOBAL.
 // SRC_LAYOUT selects how pass 0 reads shared memory: 0 the swizzled column
 // layout swz(), 1 the row-side box layout of the tensor copies.
 template <int L, int DIR, int THREADS, bool SRC_GLOBAL, bool DST_GLOBAL, bool INPLACE_GLOBAL, int PASS = 0,
-          int SRC_LAYOUT = 0>
+          int SRC_LAYOUT = 0, int PREC = kPrecFP32>
 __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const TileIO& io) {
   constexpr int NP = make_radices(L).n;
   if constexpr (PASS < NP) {
@@ -471,8 +671,12 @@ __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const T
     // before overwriting shared memory, everyone must have read it; a direct
     // global->global single pass in place also needs the barrier
     constexpr bool sync_w = (!src_g && !dst_g) || (src_g && dst_g && INPLACE_GLOBAL);
-    stockham_pass<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, PASS == 0 ? SRC_LAYOUT : 0>(sm, tw, io);
-    fft_passes<L, DIR, THREADS, SRC_GLOBAL, DST_GLOBAL, INPLACE_GLOBAL, PASS + 1, SRC_LAYOUT>(sm, tw, io);
+    if constexpr (PREC != kPrecFP32 && make_radices(L).r[PASS] == 16 && (PASS > 0 || SRC_LAYOUT == 0)) {
+      stockham_pass_tc16<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, PREC>(sm, tw, io);
+    } else {
+      stockham_pass<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, PASS == 0 ? SRC_LAYOUT : 0>(sm, tw, io);
+    }
+    fft_passes<L, DIR, THREADS, SRC_GLOBAL, DST_GLOBAL, INPLACE_GLOBAL, PASS + 1, SRC_LAYOUT, PREC>(sm, tw, io);
   }
 }
 
@@ -587,7 +791,7 @@ __device__ __forceinline__ TileIO make_io(const StageDesc& d, long long tile, in
 // Process one tile of one stage. THREADS may exceed threads_for(L) (the
 // persistent kernel runs several lengths with one block size); the extra
 // groups then share the butterflies.
-template <int L, int DIR, int KIND, int THREADS>
+template <int L, int DIR, int KIND, int THREADS, int PREC = kPrecFP32>
 __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile, float2* sm, const float2* tw,
                                              const float2* tw2) {
   int o, g0;
@@ -607,19 +811,19 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
       row_load<THREADS, L>(sm, io);
       __syncthreads();
       if (row_out) {
-        fft_passes<L, DIR, THREADS, false, false, false>(sm, tw, io);
+        fft_passes<L, DIR, THREADS, false, false, false, 0, 0, PREC>(sm, tw, io);
         row_store<THREADS, L>(sm, io);
       } else {
-        fft_passes<L, DIR, THREADS, false, true, false>(sm, tw, io);
+        fft_passes<L, DIR, THREADS, false, true, false, 0, 0, PREC>(sm, tw, io);
       }
     } else {
       if (row_out) {
-        fft_passes<L, DIR, THREADS, true, false, false>(sm, tw, io);
+        fft_passes<L, DIR, THREADS, true, false, false, 0, 0, PREC>(sm, tw, io);
         row_store<THREADS, L>(sm, io);
       } else if (inplace) {
-        fft_passes<L, DIR, THREADS, true, true, true>(sm, tw, io);
+        fft_passes<L, DIR, THREADS, true, true, true, 0, 0, PREC>(sm, tw, io);
       } else {
-        fft_passes<L, DIR, THREADS, true, true, false>(sm, tw, io);
+        fft_passes<L, DIR, THREADS, true, true, false, 0, 0, PREC>(sm, tw, io);
       }
     }
   } else if constexpr (KIND == kR2CPost) {

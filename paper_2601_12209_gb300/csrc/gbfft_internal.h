@@ -24,6 +24,15 @@ enum TileKind : int {
   kPoissonZ = 4,  // forward FFT, multiply by -1/|k|^2, inverse FFT (fused Poisson z stage)
 };
 
+// Arithmetic of a stage's radix-16 passes: FP32 on the CUDA cores, or dense
+// 16x16 DFT products on the tensor cores with operands split into hi/lo pairs
+// of FP16 or BF16 (FP32 accumulation). Storage is complex64 in every mode.
+enum StagePrec : int {
+  kPrecFP32 = 0,
+  kPrecF16Split = 1,
+  kPrecBF16Split = 2,
+};
+
 // Dependency rule of a tile on the previous stage of the same launch
 // (persistent kernel only). See DepRule handling in the persistent kernel.
 enum DepRule : int {
@@ -66,6 +75,7 @@ struct StageDesc {
   // persistent-kernel dependency rule on the previous stage
   int dep_rule;
   int prev_n_outer, prev_n_gchunks;
+  int prec;  // StagePrec of the radix-16 passes (kPlain stages of staged launches)
 };
 
 // Control block of one persistent launch (device memory, zeroed before each launch).

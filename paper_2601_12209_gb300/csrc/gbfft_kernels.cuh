@@ -12,6 +12,7 @@ namespace gbfft {
 
 struct StageKernel {
   int L, dir, kind;
+  int prec;  // StagePrec of the radix-16 passes
   const void* fn;
   int threads;
   size_t smem;
@@ -55,8 +56,14 @@ constexpr size_t stage_smem_bytes() {
 // it does not; the hardware block scheduler then hands out the tiles.
 __host__ __device__ constexpr bool stage_loops(int L) { return (L & (L - 1)) == 0; }
 
-template <int L, int DIR, int KIND>
-__global__ void __launch_bounds__(threads_for(L), min_blocks_for(L)) stage_kernel(StageDesc d) {
+// The tensor-core passes hold a column group's accumulators across the
+// pass's barrier as well as the DFT-16 operand fragments: one block fewer.
+__host__ __device__ constexpr int stage_min_blocks(int L, int prec) {
+  return prec == kPrecFP32 ? min_blocks_for(L) : (min_blocks_for(L) > 1 ? min_blocks_for(L) - 1 : 1);
+}
+
+template <int L, int DIR, int KIND, int PREC = kPrecFP32>
+__global__ void __launch_bounds__(threads_for(L), stage_min_blocks(L, PREC)) stage_kernel(StageDesc d) {
   constexpr int THREADS = threads_for(L);
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
@@ -67,18 +74,19 @@ __global__ void __launch_bounds__(threads_for(L), min_blocks_for(L)) stage_kerne
   __syncthreads();
   if constexpr (stage_loops(L)) {
     for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
-      process_tile<L, DIR, KIND, THREADS>(d, tile, sm, tw, tw2);
+      process_tile<L, DIR, KIND, THREADS, PREC>(d, tile, sm, tw, tw2);
       __syncthreads();
     }
   } else {
-    if ((long long)blockIdx.x < d.n_tiles) process_tile<L, DIR, KIND, THREADS>(d, (long long)blockIdx.x, sm, tw, tw2);
+    if ((long long)blockIdx.x < d.n_tiles)
+      process_tile<L, DIR, KIND, THREADS, PREC>(d, (long long)blockIdx.x, sm, tw, tw2);
   }
 }
 
-template <int L, int DIR, int KIND>
+template <int L, int DIR, int KIND, int PREC = kPrecFP32>
 StageKernel make_stage_entry() {
-  return StageKernel{L, DIR, KIND, reinterpret_cast<const void*>(&stage_kernel<L, DIR, KIND>), threads_for(L),
-                     stage_smem_bytes<L, KIND>(), stage_loops(L)};
+  return StageKernel{L, DIR, KIND, PREC, reinterpret_cast<const void*>(&stage_kernel<L, DIR, KIND, PREC>),
+                     threads_for(L), stage_smem_bytes<L, KIND>(), stage_loops(L)};
 }
 
 // ----------------------------------------------------- persistent kernel

@@ -22,6 +22,8 @@ namespace gbfft {
 struct ManySegment {
   StageDesc d;
   int in_buf, out_buf;  // 0 in, 1 out, 2 workspace
+  // counters the consumer segment reads (kSig* bits); the others are not written
+  int sig_mask, sig_pad;
   long long in_off, out_off;
   // counters of this segment (offsets into the launch's counter buffer)
   long long c_outer, c_outer16, c_gchunk, c_total, c_stage;
@@ -50,6 +52,7 @@ struct ManyArgs {
   unsigned int ticket_base;
 };
 
+constexpr int kSigOuter16 = 1, kSigGchunk = 2, kSigStage = 4;
 constexpr int kManyThreads = 256;
 constexpr int kManyMaxSegs = 256;  // 3 stages x up to 85 grids per launch
 
@@ -103,12 +106,11 @@ __device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment
   const int b = (int)(rest / (unsigned)d.n_outer);
   const int n16 = (d.n_outer + kTileP - 1) / kTileP;
   unsigned int* C = a.counters;
+  if (!m.sig_mask) return;  // last stage of its grid: nobody waits on it
   __threadfence();
-  atomicAdd(C + m.c_outer + (long long)b * d.n_outer + o, 1u);
-  atomicAdd(C + m.c_outer16 + (long long)b * n16 + o / kTileP, 1u);
-  atomicAdd(C + m.c_gchunk + (long long)b * d.n_gchunks + gc, 1u);
-  atomicAdd(C + m.c_total + b, 1u);
-  atomicAdd(C + m.c_stage, 1u);
+  if (m.sig_mask & kSigOuter16) atomicAdd(C + m.c_outer16 + (long long)b * n16 + o / kTileP, 1u);
+  if (m.sig_mask & kSigGchunk) atomicAdd(C + m.c_gchunk + (long long)b * d.n_gchunks + gc, 1u);
+  if (m.sig_mask & kSigStage) atomicAdd(C + m.c_stage, 1u);
 }
 
 // One ticket per block: the block takes the next ticket, finds its segment,

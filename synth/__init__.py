@@ -123,3 +123,48 @@ def plane_wave_spec(n: int, seed: int, count: int = 16) -> tuple[np.ndarray, np.
     mags = (torch.arange(count, dtype=torch.float64) + 1.0) / 4.0
     a = (mags * torch.cos(phases)).numpy() + 1j * (mags * torch.sin(phases)).numpy()
     return np.asarray(ks, dtype=np.int64), a.astype(np.complex128)
+
+
+def uniform_complex_slabs(shape, seed: int, planes: int = 64) -> torch.Tensor:
+    """complex64 grid [nz][ny][nx] with Re, Im i.i.d. uniform[-1, 1], drawn slab by slab.
+
+    Slab s (z-planes [s*planes, (s+1)*planes)) draws Re then Im in fp64 from a
+    generator seeded with seed * 1_000_003 + s, so a 2^30-point grid never
+    needs an fp64 copy of the whole grid.
+    """
+    nz, ny, nx = (int(s) for s in shape)
+    out = torch.empty((nz, ny, nx), dtype=torch.complex64)
+    view = torch.view_as_real(out)
+    for s, z0 in enumerate(range(0, nz, planes)):
+        z1 = min(nz, z0 + planes)
+        g = _gen(int(seed) * 1_000_003 + s)
+        view[z0:z1, ..., 0] = (torch.rand((z1 - z0, ny, nx), generator=g, dtype=torch.float64) * 2.0 - 1.0).float()
+        view[z0:z1, ..., 1] = (torch.rand((z1 - z0, ny, nx), generator=g, dtype=torch.float64) * 2.0 - 1.0).float()
+    return out
+
+
+def add_plane_waves(grid: torch.Tensor, ks: np.ndarray, amps: np.ndarray, planes: int = 64) -> torch.Tensor:
+    """Add the input signal sum_m a_m exp(+2 pi i (kx x + ky y + kz z) / n) to a cubic
+    complex64 grid [n][n][n] in place (on the grid's device).
+
+    Each wave is built in fp64 from its integer phase (k . r) mod n, as the
+    product of its three 1D factors, and rounded once into the grid. Its 3D DFT
+    is n^3 a_m at bin k_m and zero elsewhere (up to the grid's rounding).
+    """
+    n = grid.shape[-1]
+    assert grid.shape == (n, n, n) and grid.dtype == torch.complex64
+    dev = grid.device
+    r = torch.arange(n, dtype=torch.int64, device=dev)
+
+    def factor(k):
+        ang = ((int(k) * r) % n).to(torch.float64) * (2.0 * math.pi / n)
+        return torch.complex(torch.cos(ang), torch.sin(ang))
+
+    for z0 in range(0, n, planes):
+        z1 = min(n, z0 + planes)
+        acc = torch.zeros((z1 - z0, n, n), dtype=torch.complex128, device=dev)
+        for (kx, ky, kz), a in zip(np.asarray(ks).tolist(), np.asarray(amps).tolist()):
+            ex, ey, ez = factor(kx), factor(ky), factor(kz)[z0:z1]
+            acc += (complex(a) * ez)[:, None, None] * ey[None, :, None] * ex[None, None, :]
+        grid[z0:z1] += acc.to(torch.complex64)
+    return grid

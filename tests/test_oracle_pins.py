@@ -12,6 +12,7 @@ import os
 
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import synth
@@ -279,3 +280,43 @@ def test_separable_stage_sequence():
     B = oracle.fft1(oracle.layout_a_to_b(A))
     C = oracle.fft1(oracle.layout_b_to_c(B))
     np.testing.assert_allclose(oracle.layout_c_to_a(C), np.fft.fftn(x), atol=1e-11)
+
+
+def test_dft3_bins_c64_equals_fp64_version():
+    """The threaded complex64 bin sum reads the same values and adds the same terms in the same
+    order as the FP64 one, so it agrees bit for bit; both agree with the separable FFT."""
+    x = synth.uniform_complex((6, 10, 12), seed=21)
+    nz, ny, nx = 6, 10, 12
+    bins = [(kx, ky, kz) for kz in range(nz) for ky in range(0, ny, 3) for kx in range(nx)]
+    a = oracle.dft3_bins_c64(x, bins, threads=3)
+    b = oracle.dft3_bins(x.numpy().astype(np.complex128), bins)
+    assert np.array_equal(a, b)
+    full = oracle.fft3(x.numpy())
+    ref = np.array([full[kz, ky, kx] for kx, ky, kz in bins])
+    np.testing.assert_allclose(a, ref, atol=1e-11, rtol=0)
+    with pytest.raises(ValueError):
+        oracle.dft3_bins_c64(x, [(nx, 0, 0)])
+
+
+def test_plane_waves_closed_form():
+    """Waves-only grid: the DFT is n^3 a_m at k_m and ~0 elsewhere (the 1024^3 precision pin,
+    at n = 24); also the slab-wise noise generator is deterministic and in range."""
+    n = 24
+    ks, amps = synth.plane_wave_spec(n, seed=7, count=16)
+    assert len({tuple(k) for k in ks.tolist()}) == 16
+    np.testing.assert_allclose(np.abs(amps), (np.arange(16) + 1) / 4, rtol=1e-15)
+    g = torch.zeros((n, n, n), dtype=torch.complex64)
+    synth.add_plane_waves(g, ks, amps, planes=5)
+    X = oracle.fft3(g.numpy())
+    N = n ** 3
+    peaks = np.array([X[kz, ky, kx] for kx, ky, kz in ks.tolist()])
+    np.testing.assert_allclose(peaks, N * amps, rtol=2e-7, atol=0)
+    rest = X.copy()
+    for kx, ky, kz in ks.tolist():
+        rest[kz, ky, kx] = 0
+    assert np.sqrt(np.sum(np.abs(rest) ** 2)) < 1e-6 * np.sqrt(np.sum(np.abs(peaks) ** 2))
+    np.testing.assert_allclose(oracle.dft3_bins_c64(g, ks), peaks, rtol=1e-12, atol=1e-6)
+    u = synth.uniform_complex_slabs((9, 5, 4), seed=3, planes=4)
+    assert torch.equal(u, synth.uniform_complex_slabs((9, 5, 4), seed=3, planes=4))
+    r = torch.view_as_real(u)
+    assert float(r.abs().max()) <= 1.0 and u.dtype == torch.complex64
