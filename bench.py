@@ -253,7 +253,8 @@ def main():
     ap.add_argument("--tma-mask-inv", type=int, default=0, help="with --launch staged: tensor-copy stages (bits)")
     ap.add_argument("--ncu-case", default=None,
                     help="run one 512^3 case for a profiler and exit: staged_r2c, staged_lsu_r2c, persistent_r2c, "
-                         "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c")
+                         "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024 / "
+                         "split_bf16_1024 (C2C 1024x512x64 with tensor-core radix-16 passes)")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -428,10 +429,17 @@ def ncu_case(name):
     import paper_2601_12209_gb300 as gb
     from paper_2601_12209_gb300 import _build, abi
     _build.build()
-    kind = "r2c" if name.endswith("r2c") else "c2c"
-    plan = gb.Plan(N, N, N, kind=kind, staged=name.startswith("staged"), slab=name.startswith("slab"),
-                   tma="_lsu" not in name)
-    x = (synth.normal_real((N, N, N), seed=2) if kind == "r2c" else synth.uniform_complex((N, N, N), seed=3)).cuda()
+    if name.startswith("split_"):
+        # split_<fp16|bf16>_1024: C2C 1024 x 512 x 64 (268 MB per buffer), x stage has the tensor-core pass
+        prec = name.split("_")[1] + "_split"
+        plan = gb.Plan(1024, 512, 64, precision=prec)
+        x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
+        kind = "c2c"
+    else:
+        kind = "r2c" if name.endswith("r2c") else "c2c"
+        plan = gb.Plan(N, N, N, kind=kind, staged=name.startswith("staged"), slab=name.startswith("slab"),
+                       tma="_lsu" not in name)
+        x = (synth.normal_real((N, N, N), seed=2) if kind == "r2c" else synth.uniform_complex((N, N, N), seed=3)).cuda()
     for _ in range(3):
         y = plan.exec(abi.GBFFT_OP_FORWARD, x)
         plan.exec(abi.GBFFT_OP_INVERSE, y)

@@ -99,8 +99,9 @@ def _rel_l2_dev(a: torch.Tensor, b: torch.Tensor) -> float:
 def test_precision_1024_plane_waves(gb):
     """1024^3 C2C: uniform[-1,1] noise plus 16 plane waves (|a_m| = (m+1)/4).
 
-    Per mode: sampled bins (the 16 peaks and 16 random bins) against the FP64
-    direct sum of the same complex64 input; the waves alone against their closed
+    Per mode: sampled bins against the FP64 direct sum of the same complex64
+    input (the 16 peaks relative to their size, 16 random bins relative to the
+    spectrum's rms); the waves alone against their closed
     form n^3 a_m at k_m (and the energy that leaks elsewhere); the round trip.
     """
     n = 1024
@@ -124,7 +125,10 @@ def test_precision_1024_plane_waves(gb):
         y = p.forward(x)
         got = y[kz, ky, kx].cpu().numpy().astype(np.complex128)
         rms = float(torch.sqrt(torch.mean(torch.abs(y.to(torch.complex128)) ** 2)))
-        e_bins = float(np.max(np.abs(got - ref))) / rms
+        # a peak carries its own rounding (relative to its size); elsewhere the error is
+        # the spread of all the rounding, relative to the spectrum's rms
+        e_bins = max(float(np.max(np.abs(got[:16] - ref[:16]) / np.abs(ref[:16]))),
+                     float(np.max(np.abs(got[16:] - ref[16:]))) / rms)
         z = p.inverse(y)
         e_rt = _rel_l2_dev(z, x)
         del z
@@ -136,7 +140,7 @@ def test_precision_1024_plane_waves(gb):
             np.sqrt(np.sum(np.abs(N * amps) ** 2)))
         torch.cuda.synchronize()
         assert p.device_error() == 0
-        print(f"[precision] 1024^3 {precision}: bins max err/rms {e_bins:.3e}, peaks rel {e_peak:.3e}, "
+        print(f"[precision] 1024^3 {precision}: sampled bins {e_bins:.3e}, peaks rel {e_peak:.3e}, "
               f"leak {leak:.3e}, round trip {e_rt:.3e}")
         del y, w
         tol = TOL[precision]
