@@ -253,8 +253,9 @@ def main():
     ap.add_argument("--tma-mask-inv", type=int, default=0, help="with --launch staged: tensor-copy stages (bits)")
     ap.add_argument("--ncu-case", default=None,
                     help="run one 512^3 case for a profiler and exit: staged_r2c, staged_lsu_r2c, persistent_r2c, "
-                         "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024 / "
-                         "split_bf16_1024 (C2C 1024x512x64 with tensor-core radix-16 passes)")
+                         "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024, "
+                         "split_bf16_1024, split_fp32_1024 (C2C 1024x512x64, staged thread-load launches; "
+                         "tensor-core radix-16 passes unless fp32)")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -431,8 +432,8 @@ def ncu_case(name):
     _build.build()
     if name.startswith("split_"):
         # split_<fp16|bf16>_1024: C2C 1024 x 512 x 64 (268 MB per buffer), x stage has the tensor-core pass
-        prec = name.split("_")[1] + "_split"
-        plan = gb.Plan(1024, 512, 64, precision=prec)
+        prec = name.split("_")[1]
+        plan = gb.Plan(1024, 512, 64, precision=prec if prec == "fp32" else prec + "_split", staged=True, tma=False)
         x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
         kind = "c2c"
     else:
