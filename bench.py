@@ -72,13 +72,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# the sources of the stage and tensor-copy kernels' device code
+KERNEL_SOURCES = ("gbfft_internal.h", "gbfft_device.cuh", "gbfft_kernels.cuh", "gbfft_tma.cuh")
+# ... and of the fused plane kernels
+PLANE_SOURCES = KERNEL_SOURCES + ("gbfft_plane.cuh",)
+
+
+def kernel_source_hash(files=KERNEL_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_12209_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -90,7 +95,10 @@ def ncu_traffic(kernel_key):
     try:
         with open(p) as fh:
             d = json.load(fh)
-        if d.get("source_hash") != kernel_source_hash():
+        if "plane" in kernel_key:
+            if d.get("plane_source_hash") != kernel_source_hash(PLANE_SOURCES):
+                return None
+        elif d.get("source_hash") != kernel_source_hash():
             return None
         v = d.get("kernels", {}).get(kernel_key)
         return float(v) if v is not None else None

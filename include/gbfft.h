@@ -67,7 +67,9 @@ typedef struct gbfft_plan_s* gbfft_plan;
 
 /* plan flags */
 #define GBFFT_PENCIL 0u          /* three stages, two redistributions (Algorithm 1) */
-#define GBFFT_SLAB 1u            /* x and y per z-plane, then z (Section III-A) */
+#define GBFFT_SLAB 1u            /* x and y per z-plane, then z (Section III-A); the x,y pair runs
+                                    as one fused plane launch where built (512^2, 256^2 planes)
+                                    unless GBFFT_STAGED */
 #define GBFFT_TRANSPOSED_OUT 2u  /* pencil only: forward leaves C[b][kx][ky][kz] ("collect from C",
                                     Algorithm 1); inverse then reads that layout */
 #define GBFFT_STAGED 4u          /* one launch per stage instead of one persistent launch */
@@ -157,9 +159,11 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
  * For each pipeline of the plan -- 0 forward (FORWARD, INVERSE_ADJOINT),
  * 1 inverse (INVERSE, ADJOINT), 2 Poisson (R2C plans) -- it times on
  * `stream`, with CUDA events, every stage with the thread-load kernel and
- * with the tensor-copy kernel (where one applies), and the whole pipeline as
- * one persistent launch (where a kernel family exists); it keeps the fastest
- * per-stage choice or the persistent launch, whichever is faster. Later exec
+ * with the tensor-copy kernel (where one applies), the whole pipeline as
+ * one persistent launch (where a kernel family exists) and, for slab plans,
+ * each in-plane stage pair as one fused plane launch (a thread-block cluster
+ * per xy-plane runs both stages while the plane is in L2); it keeps the
+ * fastest. Later exec
  * calls use the choice. Blocking (synchronises `stream`); allocates the
  * plan's workspace and two scratch buffers on first use; respects
  * GBFFT_STAGED and GBFFT_NO_TMA. Do not call it during stream capture.
@@ -167,7 +171,8 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
 int gbfft_plan_autotune(gbfft_plan plan, void* stream);
 /*
  * The tuned choice of a pipeline (0, 1, 2 as above): *tuned 0/1,
- * *persistent 0/1, *tma_mask bit s = stage s uses the tensor-copy kernel,
+ * *persistent 0/1, *tma_mask bit s (0-7) = stage s uses the tensor-copy
+ * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch,
  * *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
  * staged candidates. Any output pointer may be NULL.
  */
@@ -177,7 +182,8 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
  * Fix a pipeline's launch choice by hand (as gbfft_plan_autotune would):
  * persistent 1 = one persistent launch (when a kernel family exists), else
  * staged launches with bit s of tma_mask selecting the tensor-copy kernel for
- * stage s (where it applies).
+ * stage s (where it applies) and bit 8 + s fusing stages s and s+1 into one
+ * plane launch (where they are a slab plan's in-plane pair).
  */
 int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask);
 /*

@@ -16,6 +16,7 @@
 #include "../../include/gbfft.h"
 #include "gbfft_kernels.cuh"
 #include "gbfft_many.cuh"
+#include "gbfft_plane.cuh"
 
 namespace gbfft {
 
@@ -36,7 +37,12 @@ void register_persistent_group_1(std::vector<PersistentKernel>&);
 void register_tma_group_0(std::vector<TmaKernel>&);
 void register_tma_group_1(std::vector<TmaKernel>&);
 void register_tma_group_2(std::vector<TmaKernel>&);
+void register_plane_group_0(std::vector<PlaneKernel>&);
 
+std::vector<PlaneKernel>& plane_registry() {
+  static std::vector<PlaneKernel> v;
+  return v;
+}
 std::vector<StageKernel>& stage_registry() {
   static std::vector<StageKernel> v;
   return v;
@@ -73,6 +79,7 @@ static void ensure_registry() {
     register_tma_group_0(t);
     register_tma_group_1(t);
     register_tma_group_2(t);
+    register_plane_group_0(plane_registry());
   });
 }
 
@@ -265,6 +272,7 @@ struct gbfft_plan_s {
     bool tuned = false;
     bool persistent = false;
     unsigned tma_mask = 0;  // bit s: stage s uses the tensor-copy kernel
+    unsigned plane_mask = 0;  // bit s: stages s and s+1 run as one fused plane launch
     float ms = 0.f;         // measured time of the chosen launch(es)
     float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
   } tune[3];
@@ -635,11 +643,78 @@ static void record_event(gbfft_plan_s* p, cudaStream_t stream, int pipe, bool fi
 
 static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream);
 
+// The fused plane kernel for stages s and s+1, if they are the two in-plane
+// stages of a slab pipeline (stage s+1 reads only stage s's tiles of the same
+// plane: rule kDepOuter over the same batch x outer planes) and one is built.
+static const PlaneKernel* find_plane(const Pipeline& P, int s) {
+  if (s + 1 >= P.n) return nullptr;
+  const StageDesc& a = P.st[s];
+  const StageDesc& b = P.st[s + 1];
+  if (b.dep_rule != kDepOuter || a.batch != b.batch || a.n_outer != b.n_outer) return nullptr;
+  if (a.prec != kPrecFP32 || b.prec != kPrecFP32 || a.n_tiles == 0 || b.n_tiles == 0) return nullptr;
+  ensure_registry();
+  for (const auto& k : plane_registry())
+    if (k.L1 == a.L && k.dir1 == a.dir && k.kind1 == a.kind && k.L2 == b.L && k.dir2 == b.dir && k.kind2 == b.kind)
+      return &k;
+  return nullptr;
+}
+
+// Bit s set for every stage s that starts a fusable in-plane pair.
+static unsigned plane_mask_of(const Pipeline& P) {
+  unsigned m = 0;
+  for (int s = 0; s + 1 < P.n; ++s)
+    if (find_plane(P, s)) {
+      m |= 1u << s;
+      ++s;
+    }
+  return m;
+}
+
+// One cluster per plane: 8 CTAs for planes above 1.5 MB (C2C 512^2), else 4,
+// and no more CTAs than the larger stage has group chunks.
+static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDesc& b, cudaStream_t stream) {
+  const long long plane_bytes = (long long)a.n_group * a.n_out * (long long)sizeof(float2);
+  int cx = plane_bytes > (3LL << 19) ? 8 : 4;
+  while (cx > 1 && cx > std::max(a.n_gchunks, b.n_gchunks)) cx /= 2;
+  const long long planes = (long long)a.batch * a.n_outer;
+  if (planes * cx > 0x7FFFFFFFLL) return GBFFT_ERR_INVALID_ARG;
+  int bpsm = 1;
+  cudaError_t e = launch_info(k->fn, k->threads, k->smem, &bpsm);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(planes * cx));
+  cfg.blockDim = dim3((unsigned)k->threads);
+  cfg.dynamicSmemBytes = k->smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cx;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  StageDesc da = a, db = b;
+  void* args[] = {&da, &db};
+  return cuda_err(cudaLaunchKernelExC(&cfg, k->fn, args));
+}
+
 // Staged launches with an explicit per-stage kernel choice (bit s of tma_mask:
-// tensor-copy kernel for stage s when it can run there).
-static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe) {
+// tensor-copy kernel for stage s when it can run there; bit s of plane_mask:
+// stages s and s+1 as one fused plane launch when they form an in-plane pair).
+static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe,
+                      unsigned plane_mask = 0) {
   record_event(p, stream, pipe, true);
   for (int s = 0; s < P.n; ++s) {
+    if ((plane_mask >> s) & 1u) {
+      if (const PlaneKernel* k = find_plane(P, s)) {
+        int rc = launch_plane(k, P.st[s], P.st[s + 1], stream);
+        if (rc) return rc;
+        record_event(p, stream, pipe, false);
+        ++s;
+        continue;
+      }
+    }
     const unsigned f = ((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA;
     int rc = launch_stage(P.st[s], stream, f, &p->ctl->error);
     if (rc) return rc;
@@ -659,9 +734,12 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
       record_event(p, stream, pipe, false);
       return rc;
     }
-    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe);
+    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe, p->tune[pipe].plane_mask);
   }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
+  // slab pipelines: the in-plane stage pairs as fused plane launches unless staged
+  const unsigned pm = (!staged && is_slab(p)) ? plane_mask_of(P) : 0u;
+  if (pm) return run_staged(p, P, (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu, stream, pipe, pm);
   const PersistentKernel* pk = staged ? nullptr : find_persistent(P);
   if (!pk) return run_staged(p, P, (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu, stream, pipe);
   record_event(p, stream, pipe, true);
@@ -1160,6 +1238,16 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
         t.ms = tp;
       }
     }
+    const unsigned pm = (plan->flags & GBFFT_STAGED) ? 0u : plane_mask_of(P);
+    if (pm) {
+      const unsigned tm = t.tma_mask;
+      float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm); }, st, reps);
+      if (tf >= 0.f && tf < t.ms) {
+        t.persistent = false;
+        t.plane_mask = pm;
+        t.ms = tf;
+      }
+    }
     t.tuned = true;
     plan->tune[pipe] = t;
   }
@@ -1173,7 +1261,7 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   const gbfft_plan_s::Tuning& t = plan->tune[pipeline];
   if (tuned) *tuned = t.tuned ? 1 : 0;
   if (persistent) *persistent = t.persistent ? 1 : 0;
-  if (tma_mask) *tma_mask = t.tma_mask;
+  if (tma_mask) *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8);
   if (ms) *ms = t.ms;
   if (stage_ms)
     for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
@@ -1185,7 +1273,8 @@ int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigne
   gbfft_plan_s::Tuning& t = plan->tune[pipeline];
   t.tuned = true;
   t.persistent = persistent != 0;
-  t.tma_mask = tma_mask;
+  t.tma_mask = tma_mask & 0xFFu;
+  t.plane_mask = (tma_mask >> 8) & 0xFFu;
   t.ms = 0.f;
   for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;
   return GBFFT_OK;
