@@ -609,6 +609,16 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
                            "gflops": 2 * flops_5n(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9,
                            "alg_gbs": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9}
     p.close()
+    p = gb.Plan(N, N, N, kind="r2c", slab=True)
+    tz = p.autotune(stream)
+    med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+    out["r2c_512_slab_tuned"] = {"fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
+                                 "gflops": 2 * flops_5n(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9,
+                                 "alg_gbs": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9,
+                                 "frac": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9 / measured_peaks()[0],
+                                 "tuning": {k: {"persistent": v["persistent"], "tma_mask": v["tma_mask"] & 0xFF,
+                                                "plane_mask": v["tma_mask"] >> 8} for k, v in tz.items()}}
+    p.close()
     p = gb.Plan(N, N, N, kind="r2c")
     med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_ADJOINT], steps, warmup, stream)
     out["r2c_512_fwd_adjoint_ms"] = med[0] + med[1]
