@@ -617,8 +617,18 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
                                  "alg_gbs": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9,
                                  "frac": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9 / measured_peaks()[0],
                                  "tuning": {k: {"persistent": v["persistent"], "tma_mask": v["tma_mask"] & 0xFF,
-                                                "plane_mask": v["tma_mask"] >> 8} for k, v in tz.items()}}
+                                                "plane_mask": (v["tma_mask"] >> 8) & 0xFF,
+                                                "plane_cx": v["tma_mask"] >> 16} for k, v in tz.items()}}
     p.close()
+    fused = {}
+    for cx in (2, 4, 8):
+        p = gb.Plan(N, N, N, kind="r2c", slab=True)
+        abi.gbfft_plan_set_tuning(p.handle, 0, False, (1 << 8) | (cx << 16))  # x,y fused; z thread loads
+        abi.gbfft_plan_set_tuning(p.handle, 1, False, (2 << 8) | (cx << 16))  # z; y,x fused
+        med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+        fused[f"cluster_{cx}"] = {"fwd_ms": med[0], "inv_ms": med[1]}
+        p.close()
+    out["r2c_512_slab_fused_plane"] = fused
     p = gb.Plan(N, N, N, kind="r2c")
     med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_ADJOINT], steps, warmup, stream)
     out["r2c_512_fwd_adjoint_ms"] = med[0] + med[1]

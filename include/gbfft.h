@@ -172,8 +172,9 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
 /*
  * The tuned choice of a pipeline (0, 1, 2 as above): *tuned 0/1,
  * *persistent 0/1, *tma_mask bit s (0-7) = stage s uses the tensor-copy
- * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch,
- * *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
+ * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch, bits
+ * 16-19 = CTAs per plane cluster of those launches (2, 4, 8; 0 = by plane
+ * size), *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
  * staged candidates. Any output pointer may be NULL.
  */
 int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask, float* ms,
@@ -182,8 +183,9 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
  * Fix a pipeline's launch choice by hand (as gbfft_plan_autotune would):
  * persistent 1 = one persistent launch (when a kernel family exists), else
  * staged launches with bit s of tma_mask selecting the tensor-copy kernel for
- * stage s (where it applies) and bit 8 + s fusing stages s and s+1 into one
- * plane launch (where they are a slab plan's in-plane pair).
+ * stage s (where it applies), bit 8 + s fusing stages s and s+1 into one
+ * plane launch (where they are a slab plan's in-plane pair) and bits 16-19
+ * the CTAs per plane cluster (2, 4 or 8; 0 = by plane size).
  */
 int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask);
 /*

@@ -273,6 +273,7 @@ struct gbfft_plan_s {
     bool persistent = false;
     unsigned tma_mask = 0;  // bit s: stage s uses the tensor-copy kernel
     unsigned plane_mask = 0;  // bit s: stages s and s+1 run as one fused plane launch
+    int plane_cx = 0;         // CTAs per plane cluster of the fused launches (0: by plane size)
     float ms = 0.f;         // measured time of the chosen launch(es)
     float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
   } tune[3];
@@ -670,11 +671,13 @@ static unsigned plane_mask_of(const Pipeline& P) {
   return m;
 }
 
-// One cluster per plane: 8 CTAs for planes above 1.5 MB (C2C 512^2), else 4,
-// and no more CTAs than the larger stage has group chunks.
-static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDesc& b, cudaStream_t stream) {
+// One cluster per plane: `cx` CTAs (2, 4 or 8; 0 picks 8 for planes above
+// 1.5 MB, as C2C 512^2, else 4), and no more CTAs than the larger stage has
+// group chunks.
+static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDesc& b, cudaStream_t stream,
+                        int cx = 0) {
   const long long plane_bytes = (long long)a.n_group * a.n_out * (long long)sizeof(float2);
-  int cx = plane_bytes > (3LL << 19) ? 8 : 4;
+  if (cx != 2 && cx != 4 && cx != 8) cx = plane_bytes > (3LL << 19) ? 8 : 4;
   while (cx > 1 && cx > std::max(a.n_gchunks, b.n_gchunks)) cx /= 2;
   const long long planes = (long long)a.batch * a.n_outer;
   if (planes * cx > 0x7FFFFFFFLL) return GBFFT_ERR_INVALID_ARG;
@@ -703,12 +706,12 @@ static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDes
 // tensor-copy kernel for stage s when it can run there; bit s of plane_mask:
 // stages s and s+1 as one fused plane launch when they form an in-plane pair).
 static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe,
-                      unsigned plane_mask = 0) {
+                      unsigned plane_mask = 0, int plane_cx = 0) {
   record_event(p, stream, pipe, true);
   for (int s = 0; s < P.n; ++s) {
     if ((plane_mask >> s) & 1u) {
       if (const PlaneKernel* k = find_plane(P, s)) {
-        int rc = launch_plane(k, P.st[s], P.st[s + 1], stream);
+        int rc = launch_plane(k, P.st[s], P.st[s + 1], stream, plane_cx);
         if (rc) return rc;
         record_event(p, stream, pipe, false);
         ++s;
@@ -734,7 +737,7 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
       record_event(p, stream, pipe, false);
       return rc;
     }
-    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe, p->tune[pipe].plane_mask);
+    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe, p->tune[pipe].plane_mask, p->tune[pipe].plane_cx);
   }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
   // slab pipelines: the in-plane stage pairs as fused plane launches unless staged
@@ -1241,11 +1244,14 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
     const unsigned pm = (plan->flags & GBFFT_STAGED) ? 0u : plane_mask_of(P);
     if (pm) {
       const unsigned tm = t.tma_mask;
-      float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm); }, st, reps);
-      if (tf >= 0.f && tf < t.ms) {
-        t.persistent = false;
-        t.plane_mask = pm;
-        t.ms = tf;
+      for (int cx : {2, 4, 8}) {
+        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx); }, st, reps);
+        if (tf >= 0.f && tf < t.ms) {
+          t.persistent = false;
+          t.plane_mask = pm;
+          t.plane_cx = cx;
+          t.ms = tf;
+        }
       }
     }
     t.tuned = true;
@@ -1261,7 +1267,7 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   const gbfft_plan_s::Tuning& t = plan->tune[pipeline];
   if (tuned) *tuned = t.tuned ? 1 : 0;
   if (persistent) *persistent = t.persistent ? 1 : 0;
-  if (tma_mask) *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8);
+  if (tma_mask) *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8) | ((unsigned)(t.plane_cx & 0xF) << 16);
   if (ms) *ms = t.ms;
   if (stage_ms)
     for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
@@ -1275,6 +1281,7 @@ int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigne
   t.persistent = persistent != 0;
   t.tma_mask = tma_mask & 0xFFu;
   t.plane_mask = (tma_mask >> 8) & 0xFFu;
+  t.plane_cx = (int)((tma_mask >> 16) & 0xFu);
   t.ms = 0.f;
   for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;
   return GBFFT_OK;
