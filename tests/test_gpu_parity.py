@@ -294,12 +294,32 @@ def test_caller_workspace(gb):
 
 
 def test_exec_host_end_to_end(gb):
+    """Pinned buffers (kernels read and write host memory directly) and pageable buffers
+    (staging copies) give the device path's bits, for every op and both layouts."""
     from paper_2601_12209_gb300 import abi
     plan = gb.Plan(64, 48, 32)
     x = synth.uniform_complex((32, 48, 64), seed=51).pin_memory()
     out = torch.empty_like(x).pin_memory()
     plan.exec_host(abi.GBFFT_OP_FORWARD, x, out)
     assert err("exec_host fwd", out.numpy(), oracle.fft3(x.numpy())) < TOL
+    for kind, shape, slab in (("c2c", (64, 48, 32), False), ("r2c", (64, 64, 48), False), ("r2c", (256, 256, 8), True),
+                              ("c2c", (256, 256, 8), True)):
+        nx, ny, nz = shape
+        p = gb.Plan(nx, ny, nz, kind=kind, slab=slab)
+        src = synth.normal_real((nz, ny, nx), seed=52) if kind == "r2c" else synth.uniform_complex((nz, ny, nx), seed=52)
+        ref_f = p.forward(src.to(dev()))
+        ref_i = p.inverse(ref_f)
+        ops = [(abi.GBFFT_OP_FORWARD, src, ref_f), (abi.GBFFT_OP_INVERSE, ref_f.cpu(), ref_i),
+               (abi.GBFFT_OP_ADJOINT, ref_f.cpu(), p.adjoint(ref_f))]
+        if kind == "r2c":
+            ops.append((4, src, p.poisson(src.to(dev()))))
+        for op, hin, ref in ops:
+            for pinned in (True, False):
+                h_in = hin.contiguous().pin_memory() if pinned else hin.contiguous().clone()
+                h_out = torch.empty(ref.shape, dtype=ref.dtype)
+                h_out = h_out.pin_memory() if pinned else h_out
+                p.exec_host(op, h_in, h_out)
+                assert torch.equal(h_out, ref.cpu()), (kind, shape, slab, op, pinned)
 
 
 @pytest.mark.parametrize("kind,shape", [("c2c", (64, 48, 32)), ("r2c", (64, 64, 64)), ("c2c", (128, 128, 128))])
