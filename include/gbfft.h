@@ -146,14 +146,10 @@ int gbfft_exec_inverse_adjoint(gbfft_plan plan, const void* in, void* out, void*
 int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream);
 
 /*
- * End-to-end call on HOST buffers: runs `op` from `host_in` to `host_out`
- * and waits for completion. When both buffers are page-locked (pinned or
- * registered) and 16-byte aligned, the kernels address them directly over
- * the CPU-GPU link: the first stage reads host_in and the last stage writes
- * host_out, with the intermediate stages in HBM (no staging copies; stage 0
- * uses thread loads). Other host memory is copied to plan-owned device
- * buffers and back. Uses plan-owned device buffers (allocated on first use).
- * op may also be 4 for gbfft_exec_poisson.
+ * End-to-end call on HOST buffers: copies `host_in` to the device, runs
+ * `op`, copies the result to `host_out`, and waits for completion. Uses
+ * plan-owned device buffers (allocated on first use). Pinned host memory
+ * gives asynchronous copies. op may also be 4 for gbfft_exec_poisson.
  */
 int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out);
 

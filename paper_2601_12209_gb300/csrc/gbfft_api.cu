@@ -726,9 +726,7 @@ static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cud
   return GBFFT_OK;
 }
 
-// `no_tma`: stages (bit s) that must use thread loads whatever the tuning
-// (their input is host memory, which tensor maps do not describe here).
-static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream_t stream, unsigned no_tma = 0u) {
+static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream_t stream) {
   int vrc = validate(P);
   if (vrc) return vrc;
   if (p->tune[pipe].tuned) {
@@ -739,11 +737,10 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
       record_event(p, stream, pipe, false);
       return rc;
     }
-    return run_staged(p, P, p->tune[pipe].tma_mask & ~no_tma, stream, pipe, p->tune[pipe].plane_mask,
-                      p->tune[pipe].plane_cx);
+    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe, p->tune[pipe].plane_mask, p->tune[pipe].plane_cx);
   }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
-  const unsigned tm = ((p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu) & ~no_tma;
+  const unsigned tm = (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu;
   // slab pipelines: the in-plane stage pairs as fused plane launches unless staged
   const unsigned pm = (!staged && is_slab(p)) ? plane_mask_of(P) : 0u;
   if (pm) return run_staged(p, P, tm, stream, pipe, pm);
@@ -1018,18 +1015,6 @@ static int check_ptrs(const void* in, const void* out) {
   return GBFFT_OK;
 }
 
-// Device address of a page-locked (pinned or registered) host buffer, or
-// nullptr for any other memory.
-static void* pinned_device_ptr(const void* host) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-  return a.devicePointer;
-}
-
 static Buf ws_buf(gbfft_plan_s* p, int i) {
   if (!p->ws || i >= p->n_ws) return Buf{nullptr, 0};
   return Buf{reinterpret_cast<char*>(p->ws) + (size_t)i * spectrum_bytes(p),
@@ -1114,25 +1099,6 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
     plan->h_in_bytes = plan->h_out_bytes = big;
   }
   cudaStream_t s = plan->h_stream;
-  // Page-locked host buffers are addressable by kernels over the CPU-GPU link:
-  // the first stage then reads the input from host memory and the last stage
-  // writes the result there (no staging copies); the stages between stay in
-  // HBM. Other host memory goes through staging copies.
-  void* din = pinned_device_ptr(host_in);
-  void* dout = din ? pinned_device_ptr(host_out) : nullptr;
-  if (din && dout && (((uintptr_t)din | (uintptr_t)dout) % 16) == 0) {
-    int rc = ensure_workspace(plan);
-    if (rc) return rc;
-    const int pipe = op == 4 ? kPipePoisson : pipe_of(op);
-    Buf bin{din, (long long)(ib / sizeof(float2))};
-    Buf bout{plan->h_out_dev, (long long)(big / sizeof(float2))};
-    Pipeline P = build_pipeline(plan, pipe, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
-    P.st[P.n - 1].out = reinterpret_cast<float2*>(dout);
-    P.out_cap[P.n - 1] = (long long)(ob / sizeof(float2));
-    rc = run_pipeline(plan, P, pipe, s, 1u);
-    if (rc) return rc;
-    return cuda_err(cudaStreamSynchronize(s));
-  }
   if (cudaMemcpyAsync(plan->h_in_dev, host_in, ib, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return GBFFT_ERR_CUDA;
   int rc = op == 4 ? gbfft_exec_poisson(plan, plan->h_in_dev, plan->h_out_dev, s)
