@@ -537,11 +537,68 @@ struct Dft16Frags {
   }
 };
 
-// The radix-16 pass PASS of a length-L tile on the tensor cores. A column
-// group is 8 butterflies of one group j (pencils 8h..8h+7, h = cg & 1); lane
-// (g, t) loads inputs r = 2t, 2t+1, 2t+8, 2t+9 of butterfly (j, 8h+g) -- the
-// m16n8k16 B layout -- and receives outputs q = g, g+8 of butterflies
-// (j, 8h+2t) and (j, 8h+2t+1). Reads, barrier, writes as in stockham_pass.
+// One column group on the tensor cores: the 8 butterflies whose inputs this
+// lane holds as x[0..3] (inputs r = 2t, 2t+1, 2t+8, 2t+9 of butterfly g,
+// already twiddled). y[0..7] receives outputs (q = g, pencil 2t), (q = g,
+// pencil 2t+1), (q = g+8, pencil 2t), (q = g+8, pencil 2t+1) as re, im pairs.
+template <int PREC, int DIR>
+__device__ __forceinline__ void tc16_group(const Dft16Frags<PREC, DIR>& F, const float2 (&x)[4], float (&y)[8]) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int tq = threadIdx.x & 3;
+  // power-of-two column scale: the 4 lanes of a column reduce their maxima
+  float m = fmaxf(fmaxf(fmaxf(fabsf(x[0].x), fabsf(x[0].y)), fmaxf(fabsf(x[1].x), fabsf(x[1].y))),
+                  fmaxf(fmaxf(fabsf(x[2].x), fabsf(x[2].y)), fmaxf(fabsf(x[3].x), fabsf(x[3].y))));
+  m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
+  m = fmaxf(m, __shfl_xor_sync(kFull, m, 2));
+  int e = (int)((__float_as_uint(m) >> 23) & 0xffu);  // m in [2^(e-127), 2^(e-126))
+  e = e == 0 ? 126 : min(e, 252);                      // zero or subnormal column: scale 1
+  const float sc = __uint_as_float((uint32_t)(253 - e) << 23);  // 2^(126 - e)
+  uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
+  split16x2<PREC>(x[0].x * sc, x[1].x * sc, rh0, rl0);
+  split16x2<PREC>(x[2].x * sc, x[3].x * sc, rh1, rl1);
+  split16x2<PREC>(x[0].y * sc, x[1].y * sc, ih0, il0);
+  split16x2<PREC>(x[2].y * sc, x[3].y * sc, ih1, il1);
+  constexpr uint32_t kNeg = 0x80008000u;  // sign bits of both 16-bit halves
+  float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
+  // small terms first, then hi.hi
+  mma_16816<PREC>(yr, F.re_hi, rl0, rl1);
+  mma_16816<PREC>(yr, F.re_lo, rh0, rh1);
+  mma_16816<PREC>(yr, F.im_hi, il0 ^ kNeg, il1 ^ kNeg);
+  mma_16816<PREC>(yr, F.im_lo, ih0 ^ kNeg, ih1 ^ kNeg);
+  mma_16816<PREC>(yr, F.re_hi, rh0, rh1);
+  mma_16816<PREC>(yr, F.im_hi, ih0 ^ kNeg, ih1 ^ kNeg);
+  mma_16816<PREC>(yi, F.im_hi, rl0, rl1);
+  mma_16816<PREC>(yi, F.im_lo, rh0, rh1);
+  mma_16816<PREC>(yi, F.re_hi, il0, il1);
+  mma_16816<PREC>(yi, F.re_lo, ih0, ih1);
+  mma_16816<PREC>(yi, F.im_hi, rh0, rh1);
+  mma_16816<PREC>(yi, F.re_hi, ih0, ih1);
+  // output columns 2t and 2t+1 were scaled by the lanes 8t and 8t+4
+  const int e0 = __shfl_sync(kFull, e, 8 * tq);
+  const int e1 = __shfl_sync(kFull, e, 8 * tq + 4);
+  const float s0 = __uint_as_float((uint32_t)(e0 + 1) << 23);  // 2^(e0 - 126)
+  const float s1 = __uint_as_float((uint32_t)(e1 + 1) << 23);
+  y[0] = yr[0] * s0;
+  y[1] = yi[0] * s0;
+  y[2] = yr[1] * s1;
+  y[3] = yi[1] * s1;
+  y[4] = yr[2] * s0;
+  y[5] = yi[2] * s0;
+  y[6] = yr[3] * s1;
+  y[7] = yi[3] * s1;
+}
+
+// The radix-16 pass PASS of a length-L tile on the tensor cores. A warp takes
+// butterfly group j for all 16 pencils: two column groups of 8 butterflies
+// (pencils 8h..8h+7, h = 0, 1). Lane (g, t) loads inputs r = 2t, 2t+1, 2t+8,
+// 2t+9 of butterflies (j, 8h+g) -- the m16n8k16 B layout -- and receives
+// outputs q = g, g+8 of butterflies (j, 8h+2t) and (j, 8h+2t+1). Reads,
+// barrier, writes as in stockham_pass.
+//
+// Bank spreading: when the rows a warp touches share one swizzle phase (all
+// loads when L/16 is a multiple of 8, the stores when Ns is), lanes t >= 2 (for
+// loads) or g >= 4 (for stores) take the other half of the tile first, so every
+// access instruction splits evenly over both 16-bank halves of a 128-byte row.
 template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, bool SYNC_BEFORE_WRITE, int PREC>
 __device__ __forceinline__ void stockham_pass_tc16(float2* sm, const float2* tw, const TileIO& io) {
   constexpr int R = 16;
@@ -549,109 +606,88 @@ __device__ __forceinline__ void stockham_pass_tc16(float2* sm, const float2* tw,
   static_assert(kTileP == 16 && THREADS % 32 == 0, "two column groups of 8 pencils per tile row");
   constexpr int Ns = radix_prefix(L, PASS);
   constexpr int NB = L / R;
-  constexpr int CG = NB * 2;
   constexpr int W = THREADS / 32;
-  constexpr int CGT = (CG + W - 1) / W;
+  constexpr int JT = (NB + W - 1) / W;
   constexpr int TWO = tw_pass_offset(L, PASS);
-  constexpr unsigned kFull = 0xffffffffu;
+  constexpr bool kSpreadLoads = !SRC_GLOBAL && NB % 8 == 0;
+  constexpr bool kSpreadStores = !DST_GLOBAL && Ns % 8 == 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gq = lane >> 2, tq = lane & 3;
+  const int hl = kSpreadLoads ? (tq >> 1) : 0;
+  const int hw = kSpreadStores ? (gq >> 2) : 0;
   const Dft16Frags<PREC, DIR> F;
-  float acc[CGT][8];
-  static_for<CGT>([&](auto ic) {
+  float acc[JT][2][8];
+  static_for<JT>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    const int cg = warp + i * W;
-    if (CG % W == 0 || cg < CG) {
-      const int j = cg >> 1;
-      const int p = ((cg & 1) << 3) + gq;
-      float2 x[4];
-      static_for<4>([&](auto uc) {
-        constexpr int u = decltype(uc)::value;
+    const int j = warp + i * W;
+    if (NB % W == 0 || j < NB) {
+      // load k reads half (k >> 2) ^ hl, input u = k & 3
+      float2 ld[8];
+      static_for<8>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr int u = k & 3;
+        const int p = (((k >> 2) ^ hl) << 3) + gq;
         const int n = j + (2 * tq + (u & 1) + ((u >> 1) << 3)) * NB;
         if constexpr (SRC_GLOBAL) {
-          x[u] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
+          ld[k] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
         } else {
-          x[u] = sm[swz(n, p)];
+          ld[k] = sm[swz(n, p)];
         }
       });
+      float4 w0 = make_float4(1.f, 0.f, 1.f, 0.f), w1 = w0;
       if constexpr (Ns > 1) {
         // tw is 16-byte aligned and TWO + k R + 2t is even
         const float2* twp = tw + TWO + (j % Ns) * R + 2 * tq;
-        const float4 w0 = *reinterpret_cast<const float4*>(twp);
-        const float4 w1 = *reinterpret_cast<const float4*>(twp + 8);
-        x[0] = cmul(x[0], tw_dir<DIR>(make_float2(w0.x, w0.y)));
-        x[1] = cmul(x[1], tw_dir<DIR>(make_float2(w0.z, w0.w)));
-        x[2] = cmul(x[2], tw_dir<DIR>(make_float2(w1.x, w1.y)));
-        x[3] = cmul(x[3], tw_dir<DIR>(make_float2(w1.z, w1.w)));
+        w0 = *reinterpret_cast<const float4*>(twp);
+        w1 = *reinterpret_cast<const float4*>(twp + 8);
       }
-      // power-of-two column scale: the 4 lanes of a column reduce their maxima
-      float m = fmaxf(fmaxf(fmaxf(fabsf(x[0].x), fabsf(x[0].y)), fmaxf(fabsf(x[1].x), fabsf(x[1].y))),
-                      fmaxf(fmaxf(fabsf(x[2].x), fabsf(x[2].y)), fmaxf(fabsf(x[3].x), fabsf(x[3].y))));
-      m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
-      m = fmaxf(m, __shfl_xor_sync(kFull, m, 2));
-      int e = (int)((__float_as_uint(m) >> 23) & 0xffu);  // m in [2^(e-127), 2^(e-126))
-      e = e == 0 ? 126 : min(e, 252);                      // zero or subnormal column: scale 1
-      const float sc = __uint_as_float((uint32_t)(253 - e) << 23);  // 2^(126 - e)
-      uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
-      split16x2<PREC>(x[0].x * sc, x[1].x * sc, rh0, rl0);
-      split16x2<PREC>(x[2].x * sc, x[3].x * sc, rh1, rl1);
-      split16x2<PREC>(x[0].y * sc, x[1].y * sc, ih0, il0);
-      split16x2<PREC>(x[2].y * sc, x[3].y * sc, ih1, il1);
-      constexpr uint32_t kNeg = 0x80008000u;  // sign bits of both 16-bit halves
-      float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
-      // small terms first, then hi.hi
-      mma_16816<PREC>(yr, F.re_hi, rl0, rl1);
-      mma_16816<PREC>(yr, F.re_lo, rh0, rh1);
-      mma_16816<PREC>(yr, F.im_hi, il0 ^ kNeg, il1 ^ kNeg);
-      mma_16816<PREC>(yr, F.im_lo, ih0 ^ kNeg, ih1 ^ kNeg);
-      mma_16816<PREC>(yr, F.re_hi, rh0, rh1);
-      mma_16816<PREC>(yr, F.im_hi, ih0 ^ kNeg, ih1 ^ kNeg);
-      mma_16816<PREC>(yi, F.im_hi, rl0, rl1);
-      mma_16816<PREC>(yi, F.im_lo, rh0, rh1);
-      mma_16816<PREC>(yi, F.re_hi, il0, il1);
-      mma_16816<PREC>(yi, F.re_lo, ih0, ih1);
-      mma_16816<PREC>(yi, F.im_hi, rh0, rh1);
-      mma_16816<PREC>(yi, F.re_hi, ih0, ih1);
-      // output columns 2t and 2t+1 were scaled by the lanes 8t and 8t+4
-      const int e0 = __shfl_sync(kFull, e, 8 * tq);
-      const int e1 = __shfl_sync(kFull, e, 8 * tq + 4);
-      const float s0 = __uint_as_float((uint32_t)(e0 + 1) << 23);  // 2^(e0 - 126)
-      const float s1 = __uint_as_float((uint32_t)(e1 + 1) << 23);
-      acc[i][0] = yr[0] * s0;  // q = g, pencil 8h + 2t
-      acc[i][1] = yi[0] * s0;
-      acc[i][2] = yr[1] * s1;  // q = g, pencil 8h + 2t + 1
-      acc[i][3] = yi[1] * s1;
-      acc[i][4] = yr[2] * s0;  // q = g + 8
-      acc[i][5] = yi[2] * s0;
-      acc[i][6] = yr[3] * s1;
-      acc[i][7] = yi[3] * s1;
+      static_for<2>([&](auto hc) {
+        constexpr int h = decltype(hc)::value;
+        float2 x[4];
+        static_for<4>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          x[u] = hl ? ld[((h ^ 1) << 2) | u] : ld[(h << 2) | u];
+        });
+        if constexpr (Ns > 1) {
+          x[0] = cmul(x[0], tw_dir<DIR>(make_float2(w0.x, w0.y)));
+          x[1] = cmul(x[1], tw_dir<DIR>(make_float2(w0.z, w0.w)));
+          x[2] = cmul(x[2], tw_dir<DIR>(make_float2(w1.x, w1.y)));
+          x[3] = cmul(x[3], tw_dir<DIR>(make_float2(w1.z, w1.w)));
+        }
+        tc16_group<PREC, DIR>(F, x, acc[i][h]);
+      });
     }
   });
   if constexpr (SYNC_BEFORE_WRITE) __syncthreads();
-  static_for<CGT>([&](auto ic) {
+  static_for<JT>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
-    const int cg = warp + i * W;
-    if (CG % W == 0 || cg < CG) {
-      const int j = cg >> 1;
-      const int pc = ((cg & 1) << 3) + 2 * tq;
-      if constexpr (DST_GLOBAL) {
-        // last pass (Ns R = L): output q of group j is element j + q NB
-        const float f = io.scale;
-        static_for<4>([&](auto vc) {
-          constexpr int v = decltype(vc)::value;
-          const int pp = pc + (v & 1);
-          const int n = j + (gq + ((v >> 1) << 3)) * NB;
-          if (pp < io.valid) st_data(io.gout + pp + n * io.out_n, make_float2(acc[i][2 * v] * f, acc[i][2 * v + 1] * f));
+    const int j = warp + i * W;
+    if (NB % W == 0 || j < NB) {
+      static_for<2>([&](auto mc) {
+        constexpr int m = decltype(mc)::value;
+        float a[8];
+        static_for<8>([&](auto ec) {
+          constexpr int e = decltype(ec)::value;
+          a[e] = hw ? acc[i][m ^ 1][e] : acc[i][m][e];
         });
-      } else {
-        const int k = j % Ns;
-        const int base = (j - k) * R + k;
-        // pencils pc, pc + 1 stay adjacent under the swizzle (pc even)
-        *reinterpret_cast<float4*>(sm + swz(base + gq * Ns, pc)) =
-            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(sm + swz(base + (gq + 8) * Ns, pc)) =
-            make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-      }
+        const int pc = ((m ^ hw) << 3) + 2 * tq;
+        if constexpr (DST_GLOBAL) {
+          // last pass (Ns R = L): output q of group j is element j + q NB
+          const float f = io.scale;
+          static_for<4>([&](auto vc) {
+            constexpr int v = decltype(vc)::value;
+            const int pp = pc + (v & 1);
+            const int n = j + (gq + ((v >> 1) << 3)) * NB;
+            if (pp < io.valid) st_data(io.gout + pp + n * io.out_n, make_float2(a[2 * v] * f, a[2 * v + 1] * f));
+          });
+        } else {
+          const int k = j % Ns;
+          const int base = (j - k) * R + k;
+          // pencils pc, pc + 1 stay adjacent under the swizzle (pc even)
+          *reinterpret_cast<float4*>(sm + swz(base + gq * Ns, pc)) = make_float4(a[0], a[1], a[2], a[3]);
+          *reinterpret_cast<float4*>(sm + swz(base + (gq + 8) * Ns, pc)) = make_float4(a[4], a[5], a[6], a[7]);
+        }
+      });
     }
   });
   if constexpr (!DST_GLOBAL) __syncthreads();
