@@ -87,8 +87,11 @@ __host__ __device__ constexpr int groups_for(int L) {
   Radices R = make_radices(L);
   int mn = L;
   for (int i = 0; i < R.n; ++i) mn = (L / R.r[i]) < mn ? (L / R.r[i]) : mn;
+  // up to 32 groups (512 threads); length 1024 takes 64 (1024 threads): its
+  // 16 x 1025 tile fills shared memory, so one block per SM must carry the warps
   int g = 1;
-  while (g * 2 <= mn && g * 2 <= 32) g *= 2;
+  const int cap = L >= 1024 ? 64 : 32;
+  while (g * 2 <= mn && g * 2 <= cap) g *= 2;
   return g;
 }
 
@@ -96,9 +99,12 @@ __host__ __device__ constexpr int threads_for(int L) { return 16 * groups_for(L)
 
 // Blocks per SM the register allocation must allow: two 512-thread blocks
 // (64 registers) so one block's HBM phase overlaps the other's arithmetic;
-// length 1024 keeps one block (32 complex values per thread).
+// length 1024 runs one 1024-thread block (its tile fills shared memory).
+// Mixed-radix lengths of 512 threads (640, 768, 960: radix-3/5 butterflies
+// next to radix-16 ones) need more than 64 registers, so they take one block.
 __host__ __device__ constexpr int min_blocks_for(int L) {
-  return L >= 1024 ? 1 : (threads_for(L) >= 512 ? 2 : (threads_for(L) >= 256 ? 3 : 4));
+  return L >= 1024 ? 1
+                   : (threads_for(L) >= 512 ? ((L & (L - 1)) ? 1 : 2) : (threads_for(L) >= 256 ? 3 : 4));
 }
 
 // ---------------------------------------------------------- complex helpers

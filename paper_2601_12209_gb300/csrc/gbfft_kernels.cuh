@@ -62,9 +62,16 @@ __host__ __device__ constexpr int stage_min_blocks(int L, int prec) {
   return prec == kPrecFP32 ? min_blocks_for(L) : (min_blocks_for(L) > 1 ? min_blocks_for(L) - 1 : 1);
 }
 
+// Block size of a stage kernel: threads_for(L), except that the tensor-core
+// passes at length 1024 keep 512 threads (their accumulators and operand
+// fragments do not fit the 64 registers of a 1024-thread block).
+__host__ __device__ constexpr int stage_threads(int L, int prec) {
+  return (prec != kPrecFP32 && L >= 1024) ? 512 : threads_for(L);
+}
+
 template <int L, int DIR, int KIND, int PREC = kPrecFP32>
-__global__ void __launch_bounds__(threads_for(L), stage_min_blocks(L, PREC)) stage_kernel(StageDesc d) {
-  constexpr int THREADS = threads_for(L);
+__global__ void __launch_bounds__(stage_threads(L, PREC), stage_min_blocks(L, PREC)) stage_kernel(StageDesc d) {
+  constexpr int THREADS = stage_threads(L, PREC);
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
   float2* tw = sm + (L + 1) * kTileP;
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(threads_for(L), stage_min_blocks(L, PREC)) sta
 template <int L, int DIR, int KIND, int PREC = kPrecFP32>
 StageKernel make_stage_entry() {
   return StageKernel{L, DIR, KIND, PREC, reinterpret_cast<const void*>(&stage_kernel<L, DIR, KIND, PREC>),
-                     threads_for(L), stage_smem_bytes<L, KIND>(), stage_loops(L)};
+                     stage_threads(L, PREC), stage_smem_bytes<L, KIND>(), stage_loops(L)};
 }
 
 // ----------------------------------------------------- persistent kernel

@@ -91,7 +91,7 @@ __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
 // warps hide the arithmetic latency while the copies stream; shorter pencils
 // get two blocks per SM.
 __host__ __device__ constexpr int tma_threads(int L) {
-  return L == 512 ? 1024 : threads_for(L);
+  return L == 512 ? 1024 : (L >= 1024 ? 512 : threads_for(L));
 }
 __host__ __device__ constexpr int tma_blocks_per_sm(int L) { return L >= 512 ? 1 : 2; }
 
