@@ -365,7 +365,8 @@ def main():
         else:
             axes = ("x", "y", "z") if name == "forward" else ("z", "y", "x")
             for k, t in enumerate(seg):
-                kern = "tma_stage_kernel" if (tune["tma_mask"] >> k) & 1 else "stage_kernel"
+                kern = ("warp_stage_kernel" if (tune["tma_mask"] >> (20 + k)) & 1 else
+                        "tma_stage_kernel" if (tune["tma_mask"] >> k) & 1 else "stage_kernel")
                 segs.append((f"{name} stage {axes[k]} {kern}", t, stage_bytes[k]))
     dom = max(segs, key=lambda x: x[1])
     bytes_launch = dom[2]

@@ -174,7 +174,8 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
  * *persistent 0/1, *tma_mask bit s (0-7) = stage s uses the tensor-copy
  * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch, bits
  * 16-19 = CTAs per plane cluster of those launches (2, 4, 8; 0 = by plane
- * size), *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
+ * size), bit 20 + s = stage s runs the warp-per-pencil kernel (length 512,
+ * complex, FP32), *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
  * staged candidates. Any output pointer may be NULL.
  */
 int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask, float* ms,
@@ -184,8 +185,9 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
  * persistent 1 = one persistent launch (when a kernel family exists), else
  * staged launches with bit s of tma_mask selecting the tensor-copy kernel for
  * stage s (where it applies), bit 8 + s fusing stages s and s+1 into one
- * plane launch (where they are a slab plan's in-plane pair) and bits 16-19
- * the CTAs per plane cluster (2, 4 or 8; 0 = by plane size).
+ * plane launch (where they are a slab plan's in-plane pair), bits 16-19
+ * the CTAs per plane cluster (2, 4 or 8; 0 = by plane size) and bit 20 + s
+ * the warp-per-pencil kernel for stage s (where it is built).
  */
 int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask);
 /*

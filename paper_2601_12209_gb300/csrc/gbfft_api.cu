@@ -17,6 +17,7 @@
 #include "gbfft_kernels.cuh"
 #include "gbfft_many.cuh"
 #include "gbfft_plane.cuh"
+#include "gbfft_warp.cuh"
 
 namespace gbfft {
 
@@ -38,7 +39,12 @@ void register_tma_group_0(std::vector<TmaKernel>&);
 void register_tma_group_1(std::vector<TmaKernel>&);
 void register_tma_group_2(std::vector<TmaKernel>&);
 void register_plane_group_0(std::vector<PlaneKernel>&);
+void register_warp_group_0(std::vector<WarpKernel>&);
 
+std::vector<WarpKernel>& warp_registry() {
+  static std::vector<WarpKernel> v;
+  return v;
+}
 std::vector<PlaneKernel>& plane_registry() {
   static std::vector<PlaneKernel> v;
   return v;
@@ -80,6 +86,7 @@ static void ensure_registry() {
     register_tma_group_1(t);
     register_tma_group_2(t);
     register_plane_group_0(plane_registry());
+    register_warp_group_0(warp_registry());
   });
 }
 
@@ -253,6 +260,7 @@ struct gbfft_plan_s {
   long long Nc, NA;   // spectrum / input float2 elements per batch entry
   // twiddle tables (device)
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr, *tw2 = nullptr;
+  float2 *twn_x = nullptr, *twn_y = nullptr, *twn_z = nullptr;  // natural W_L^m tables per axis
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -273,6 +281,7 @@ struct gbfft_plan_s {
     bool persistent = false;
     unsigned tma_mask = 0;  // bit s: stage s uses the tensor-copy kernel
     unsigned plane_mask = 0;  // bit s: stages s and s+1 run as one fused plane launch
+    unsigned warp_mask = 0;   // bit s: stage s runs the warp-per-pencil kernel
     int plane_cx = 0;         // CTAs per plane cluster of the fused launches (0: by plane size)
     float ms = 0.f;         // measured time of the chosen launch(es)
     float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -508,8 +517,11 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       add(Xi, 2, 1);
     }
   }
-  for (int s = 0; s < P.n; ++s)
-    if (P.st[s].kind == kPlain) P.st[s].prec = p->dtype;  // GBFFT_*_SPLIT values equal the StagePrec values
+  for (int s = 0; s < P.n; ++s) {
+    StageDesc& d = P.st[s];
+    if (d.kind == kPlain) d.prec = p->dtype;  // GBFFT_*_SPLIT values equal the StagePrec values
+    d.twn = d.tw == p->tw_x ? p->twn_x : (d.tw == p->tw_y ? p->twn_y : (d.tw == p->tw_z ? p->twn_z : nullptr));
+  }
   return P;
 }
 
@@ -549,10 +561,35 @@ static const PersistentKernel* find_persistent(const Pipeline& P) {
   return nullptr;
 }
 
-// Launch one stage: the TMA kernel when one exists for the stage and its input
-// layout can be described by a tensor map, else the load/store kernel.
+// Internal launch flag: run the stage with the warp-per-pencil kernel where one
+// is built (length 512, complex, FP32).
+constexpr unsigned kUseWarpKernel = 1u << 30;
+
+static const WarpKernel* find_warp(const StageDesc& d) {
+  if (d.kind != kPlain || d.prec != kPrecFP32 || !d.twn) return nullptr;
+  ensure_registry();
+  for (const auto& k : warp_registry())
+    if (k.L == d.L && k.dir == d.dir) return &k;
+  return nullptr;
+}
+
+// Launch one stage: the warp-per-pencil kernel when asked for and built, the
+// TMA kernel when one exists for the stage and its input layout can be
+// described by a tensor map, else the load/store kernel.
 static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags = 0, int* err = nullptr) {
   if (d.n_tiles == 0) return GBFFT_OK;
+  if (flags & kUseWarpKernel) {
+    if (const WarpKernel* wk = find_warp(d)) {
+      int bpsm = 1;
+      cudaError_t e = launch_info(wk->fn, wk->threads, wk->smem, &bpsm);
+      if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+      const long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
+      StageDesc dd = d;
+      void* args[] = {&dd};
+      return cuda_err(cudaLaunchKernel(wk->fn, dim3((unsigned)grid), dim3((unsigned)wk->threads), args, wk->smem,
+                                       stream));
+    }
+  }
   if (!(flags & GBFFT_NO_TMA) && err && d.kind != kIdentity && d.prec == kPrecFP32) {
     const int src = d.in_mode == kRow ? 1 : 2;
     const TmaKernel* tk = find_tma(d.L, d.dir, d.kind, src);
@@ -706,7 +743,7 @@ static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDes
 // tensor-copy kernel for stage s when it can run there; bit s of plane_mask:
 // stages s and s+1 as one fused plane launch when they form an in-plane pair).
 static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe,
-                      unsigned plane_mask = 0, int plane_cx = 0) {
+                      unsigned plane_mask = 0, int plane_cx = 0, unsigned warp_mask = 0) {
   record_event(p, stream, pipe, true);
   for (int s = 0; s < P.n; ++s) {
     if ((plane_mask >> s) & 1u) {
@@ -718,7 +755,7 @@ static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cud
         continue;
       }
     }
-    const unsigned f = ((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA;
+    const unsigned f = (((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA) | (((warp_mask >> s) & 1u) ? kUseWarpKernel : 0u);
     int rc = launch_stage(P.st[s], stream, f, &p->ctl->error);
     if (rc) return rc;
     record_event(p, stream, pipe, false);
@@ -737,7 +774,8 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
       record_event(p, stream, pipe, false);
       return rc;
     }
-    return run_staged(p, P, p->tune[pipe].tma_mask, stream, pipe, p->tune[pipe].plane_mask, p->tune[pipe].plane_cx);
+    const gbfft_plan_s::Tuning& t = p->tune[pipe];
+    return run_staged(p, P, t.tma_mask, stream, pipe, t.plane_mask, t.plane_cx, t.warp_mask);
   }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
   const unsigned tm = (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu;
@@ -849,6 +887,9 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->ctl);
   cudaFree(p->h_in_dev);
   cudaFree(p->h_out_dev);
+  cudaFree(p->twn_x);
+  cudaFree(p->twn_y);
+  cudaFree(p->twn_z);
   if (p->h_stream) cudaStreamDestroy(p->h_stream);
   for (auto& c : p->timed)
     for (int k = 0; k < c.nev; ++k) cudaEventDestroy(c.ev[k]);
@@ -972,7 +1013,10 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   p->tw_x = upload_table(packed_twiddles(Lx));
   p->tw_y = upload_table(packed_twiddles(ny));
   p->tw_z = upload_table(packed_twiddles(nz));
-  bool ok = p->tw_x && p->tw_y && p->tw_z;
+  p->twn_x = upload_table(twiddle_table(Lx, Lx));
+  p->twn_y = upload_table(twiddle_table(ny, ny));
+  p->twn_z = upload_table(twiddle_table(nz, nz));
+  bool ok = p->tw_x && p->tw_y && p->tw_z && p->twn_x && p->twn_y && p->twn_z;
   if (ok && kind == GBFFT_R2C) {
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
     ok = p->tw2 != nullptr;
@@ -1230,6 +1274,15 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
           t.tma_mask |= 1u << s;
         }
       }
+      if (find_warp(d)) {
+        float tw = time_calls([&] { return launch_stage(d, st, GBFFT_NO_TMA | kUseWarpKernel, &plan->ctl->error); },
+                              st, reps);
+        if (tw >= 0.f && tw < best) {
+          best = tw;
+          t.tma_mask &= ~(1u << s);
+          t.warp_mask |= 1u << s;
+        }
+      }
       t.stage_ms[s] = best;
       staged_ms += best;
     }
@@ -1245,8 +1298,9 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
     const unsigned pm = (plan->flags & GBFFT_STAGED) ? 0u : plane_mask_of(P);
     if (pm) {
       const unsigned tm = t.tma_mask;
+      const unsigned wm = t.warp_mask;
       for (int cx : {2, 4, 8}) {
-        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx); }, st, reps);
+        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx, wm); }, st, reps);
         if (tf >= 0.f && tf < t.ms) {
           t.persistent = false;
           t.plane_mask = pm;
@@ -1268,7 +1322,9 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   const gbfft_plan_s::Tuning& t = plan->tune[pipeline];
   if (tuned) *tuned = t.tuned ? 1 : 0;
   if (persistent) *persistent = t.persistent ? 1 : 0;
-  if (tma_mask) *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8) | ((unsigned)(t.plane_cx & 0xF) << 16);
+  if (tma_mask)
+    *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8) | ((unsigned)(t.plane_cx & 0xF) << 16) |
+                ((t.warp_mask & 0xFFu) << 20);
   if (ms) *ms = t.ms;
   if (stage_ms)
     for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
@@ -1283,6 +1339,7 @@ int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigne
   t.tma_mask = tma_mask & 0xFFu;
   t.plane_mask = (tma_mask >> 8) & 0xFFu;
   t.plane_cx = (int)((tma_mask >> 16) & 0xFu);
+  t.warp_mask = (tma_mask >> 20) & 0xFFu;
   t.ms = 0.f;
   for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;
   return GBFFT_OK;

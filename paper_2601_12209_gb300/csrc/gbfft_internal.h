@@ -70,6 +70,7 @@ struct StageDesc {
   const float2* tw;    // packed per-pass twiddles of length L (tw_table_len(L) entries, device)
   const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R only)
   int tw_len;          // entries of tw
+  const float2* twn;   // natural twiddles W_L^m = exp(-2 pi i m / L), m in [0, L) (device)
   // Poisson z stage: wavenumber bookkeeping of the tile's pencils
   int pz_nx, pz_ny;    // full grid nx, ny (kx of pencil = group index, ky = outer index)
   // persistent-kernel dependency rule on the previous stage
