@@ -16,7 +16,11 @@
 //      with the partner lane (b ^ 1) by shuffles.
 // Row-side pencils are read and written by their warp directly (coalesced
 // along the row); column-side input or output goes through the shared tile
-// once (the pack / unpack of the redistribution).
+// once (the pack / unpack of the redistribution). The tile is pencil-major:
+// pencil p occupies its warp's own region (pitch 529 float2, so the 16
+// pencils of one element fall in 16 different bank pairs), which also holds
+// the warp's transpose buffer; a warp therefore never touches another warp's
+// region except in the block-wide column load and store.
 #pragma once
 #include "gbfft_kernels.cuh"
 
@@ -25,8 +29,9 @@ namespace gbfft {
 constexpr int kWarpL = 512;
 constexpr int kWarpThreads = 32 * kTileP;  // one warp per pencil of the tile
 constexpr int kWarpPitch = 33;             // row pitch (float2) of the per-warp transpose buffer
-// tile [512][16] for column-side I/O and the 16 per-warp buffers share one region
-constexpr int kWarpRegion = (kTileP * 16 * kWarpPitch > kWarpL * kTileP) ? kTileP * 16 * kWarpPitch : kWarpL * kTileP;
+constexpr int kWarpRegion = 529;           // float2 per warp: one pencil (512) or the 16 x 33 buffer (528), + 1
+static_assert(kWarpRegion >= kWarpL && kWarpRegion >= 16 * kWarpPitch && kWarpRegion % 16 == 1,
+              "a warp region holds a pencil and the transpose buffer; odd pitch spreads banks");
 
 struct WarpKernel {
   int L, dir;
@@ -37,21 +42,37 @@ struct WarpKernel {
 
 std::vector<WarpKernel>& warp_registry();
 
-constexpr size_t warp_smem_bytes() { return sizeof(float2) * ((size_t)kWarpRegion + kWarpL + 16); }
+constexpr size_t warp_smem_bytes() { return sizeof(float2) * ((size_t)kTileP * kWarpRegion + kWarpL + 16); }
+
+// Column-side load / store of the pencil-major tile: lanes run along the 16
+// pencils of one element (one 128-byte line of global memory).
+__device__ __forceinline__ void warp_col_load(float2* sm, const TileIO& io) {
+  for (int it = threadIdx.x; it < kWarpL * kTileP; it += kWarpThreads) {
+    const int p = it & 15, n = it >> 4;
+    sm[p * kWarpRegion + n] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& io) {
+  for (int it = threadIdx.x; it < kWarpL * kTileP; it += kWarpThreads) {
+    const int p = it & 15, n = it >> 4;
+    if (p < io.valid) st_data(io.gout + p + n * io.out_n, cscale(sm[p * kWarpRegion + n], io.scale));
+  }
+}
 
 template <int DIR>
 __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d) {
   constexpr unsigned kFull = 0xffffffffu;
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
-  float2* tws = sm + kWarpRegion;  // [k1][t] = W512^(t k1), forward sign
-  float2* w32 = tws + kWarpL;      // W32^k2 = W512^(16 k2)
+  float2* tws = sm + kTileP * kWarpRegion;  // [k1][t] = W512^(t k1), forward sign
+  float2* w32 = tws + kWarpL;               // W32^k2 = W512^(16 k2)
   for (int i = threadIdx.x; i < kWarpL; i += kWarpThreads) tws[i] = d.twn[(i & 31) * (i >> 5)];
   if (threadIdx.x < 16) w32[threadIdx.x] = d.twn[16 * threadIdx.x];
   __syncthreads();
   const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
   const int k1 = lane >> 1, b = lane & 1;
-  float2* wb = sm + p * (16 * kWarpPitch);
+  float2* wr = sm + p * kWarpRegion;  // this warp's pencil / transpose buffer
   const bool row_in = d.in_mode == kRow, row_out = d.out_mode == kRow;
   for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
     int o, g0;
@@ -63,20 +84,20 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
       for (int i = 0; i < 16; ++i)
         v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
     } else {
-      col_load<kWarpThreads, kWarpL>(sm, io);
+      warp_col_load(sm, io);
       __syncthreads();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = sm[swz(lane + 32 * i, p)];
-      __syncthreads();  // the per-warp buffers overwrite the tile
+      for (int i = 0; i < 16; ++i) v[i] = wr[lane + 32 * i];
+      __syncwarp();  // the transpose below overwrites this warp's pencil
     }
     dft<16, DIR>(v);
 #pragma unroll
     for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], tw_dir<DIR>(tws[k * 32 + lane]));
 #pragma unroll
-    for (int k = 0; k < 16; ++k) wb[k * kWarpPitch + lane] = v[k];
+    for (int k = 0; k < 16; ++k) wr[k * kWarpPitch + lane] = v[k];
     __syncwarp();
 #pragma unroll
-    for (int a = 0; a < 16; ++a) v[a] = wb[k1 * kWarpPitch + 2 * a + b];
+    for (int a = 0; a < 16; ++a) v[a] = wr[k1 * kWarpPitch + 2 * a + b];
     dft<16, DIR>(v);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -92,13 +113,14 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
 #pragma unroll
         for (int k = 0; k < 16; ++k) st_data(dst + (k1 + 16 * k + 256 * b) * io.out_n, cscale(v[k], io.scale));
       }
-      __syncwarp();  // this warp's buffer is reused by the next tile
+      if (!row_in) __syncthreads();  // the next column load fills every warp's region
+      else __syncwarp();             // this warp's buffer is reused by the next tile
     } else {
-      __syncthreads();  // every warp is done with its buffer
+      __syncwarp();  // every lane has read the transpose buffer
 #pragma unroll
-      for (int k = 0; k < 16; ++k) sm[swz(k1 + 16 * k + 256 * b, p)] = v[k];
+      for (int k = 0; k < 16; ++k) wr[k1 + 16 * k + 256 * b] = v[k];
       __syncthreads();
-      col_store<kWarpThreads, kWarpL>(sm, io);
+      warp_col_store(sm, io);
       __syncthreads();
     }
   }
