@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
   const int k1 = lane >> 1, b = lane & 1;
   float2* wr = sm + p * kWarpRegion;  // this warp's pencil / transpose buffer
   const bool row_in = d.in_mode == kRow, row_out = d.out_mode == kRow;
+  const bool inplace = d.in == d.out;  // in-place column stages stage the tile (their lines are rewritten)
   for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
     int o, g0;
     const TileIO io = make_io(d, tile, o, g0);
@@ -83,6 +84,14 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
+    } else if (!inplace) {
+      // column side, read-only input: each warp reads its pencil straight from
+      // global memory through the read-only L1 path; the 16 warps read the 16
+      // pencils of the same 128-byte lines, so L1 serves all but the first
+      const float2* src = io.gin + p;
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        v[i] = (p < io.valid) ? __ldg(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
     } else {
       warp_col_load(sm, io);
       __syncthreads();
@@ -113,8 +122,8 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
 #pragma unroll
         for (int k = 0; k < 16; ++k) st_data(dst + (k1 + 16 * k + 256 * b) * io.out_n, cscale(v[k], io.scale));
       }
-      if (!row_in) __syncthreads();  // the next column load fills every warp's region
-      else __syncwarp();             // this warp's buffer is reused by the next tile
+      if (!row_in && inplace) __syncthreads();  // the next column load fills every warp's region
+      else __syncwarp();                        // this warp's buffer is reused by the next tile
     } else {
       __syncwarp();  // every lane has read the transpose buffer
 #pragma unroll
