@@ -365,7 +365,8 @@ def main():
         else:
             axes = ("x", "y", "z") if name == "forward" else ("z", "y", "x")
             for k, t in enumerate(seg):
-                kern = ("warp_stage_kernel" if (tune["tma_mask"] >> (20 + k)) & 1 else
+                # the warp kernel serves the complex length-512 stages (y, z), not the real x stages
+                kern = ("warp_stage_kernel" if (tune["tma_mask"] >> (20 + k)) & 1 and axes[k] != "x" else
                         "tma_stage_kernel" if (tune["tma_mask"] >> k) & 1 else "stage_kernel")
                 segs.append((f"{name} stage {axes[k]} {kern}", t, stage_bytes[k]))
     dom = max(segs, key=lambda x: x[1])

@@ -16,11 +16,13 @@
 //      with the partner lane (b ^ 1) by shuffles.
 // Row-side pencils are read and written by their warp directly (coalesced
 // along the row); column-side input or output goes through the shared tile
-// once (the pack / unpack of the redistribution). The tile is pencil-major:
-// pencil p occupies its warp's own region (pitch 529 float2, so the 16
-// pencils of one element fall in 16 different bank pairs), which also holds
-// the warp's transpose buffer; a warp therefore never touches another warp's
-// region except in the block-wide column load and store.
+// once (the pack / unpack of the redistribution): a column-side input is read
+// with lanes along the pencils (lane (tb, q) of warp w takes t = 2w + tb of
+// pencil q), step 1 runs in that layout, and step 3 gathers pencil q into
+// warp q's region; a column-side output is written by each warp into its own
+// region and stored with lanes along the pencils. Regions are pencil-major
+// (pitch 529 float2: the 16 pencils of one element fall in 16 different bank
+// pairs) and hold the warp's transpose buffer too.
 #pragma once
 #include "gbfft_kernels.cuh"
 
@@ -44,15 +46,8 @@ std::vector<WarpKernel>& warp_registry();
 
 constexpr size_t warp_smem_bytes() { return sizeof(float2) * ((size_t)kTileP * kWarpRegion + kWarpL + 16); }
 
-// Column-side load / store of the pencil-major tile: lanes run along the 16
-// pencils of one element (one 128-byte line of global memory).
-__device__ __forceinline__ void warp_col_load(float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < kWarpL * kTileP; it += kWarpThreads) {
-    const int p = it & 15, n = it >> 4;
-    sm[p * kWarpRegion + n] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
-  }
-}
-
+// Column-side store of the pencil-major tile: lanes run along the 16 pencils
+// of one element (one 128-byte line of global memory).
 __device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& io) {
   for (int it = threadIdx.x; it < kWarpL * kTileP; it += kWarpThreads) {
     const int p = it & 15, n = it >> 4;
@@ -74,37 +69,39 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
   const int k1 = lane >> 1, b = lane & 1;
   float2* wr = sm + p * kWarpRegion;  // this warp's pencil / transpose buffer
   const bool row_in = d.in_mode == kRow, row_out = d.out_mode == kRow;
-  const bool inplace = d.in == d.out;  // in-place column stages stage the tile (their lines are rewritten)
   for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
     int o, g0;
     const TileIO io = make_io(d, tile, o, g0);
     float2 v[16];
     if (row_in) {
+      // lane t of warp p: x[t + 32 i] of pencil p (coalesced along the row)
       const float2* src = io.gin + p * io.in_g;
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
-    } else if (!inplace) {
-      // column side, read-only input: each warp reads its pencil straight from
-      // global memory through the read-only L1 path; the 16 warps read the 16
-      // pencils of the same 128-byte lines, so L1 serves all but the first
-      const float2* src = io.gin + p;
+      dft<16, DIR>(v);
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], tw_dir<DIR>(tws[k * 32 + lane]));
+#pragma unroll
+      for (int k = 0; k < 16; ++k) wr[k * kWarpPitch + lane] = v[k];
+      __syncwarp();
+    } else {
+      // column side: lane (tb, q) of warp w takes t = 2w + tb of pencil q, so
+      // the 16 lanes of a half-warp read one 128-byte line; step 1 then runs
+      // in this layout and the result goes to pencil q's region
+      const int pq = lane & 15, t = 2 * p + (lane >> 4);
+      const float2* src = io.gin + pq;
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        v[i] = (p < io.valid) ? __ldg(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
-    } else {
-      warp_col_load(sm, io);
+        v[i] = (pq < io.valid) ? ld_data(src + (t + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
+      dft<16, DIR>(v);
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], tw_dir<DIR>(tws[k * 32 + t]));
+      float2* rq = sm + pq * kWarpRegion;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) rq[k * kWarpPitch + t] = v[k];
       __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = wr[lane + 32 * i];
-      __syncwarp();  // the transpose below overwrites this warp's pencil
     }
-    dft<16, DIR>(v);
-#pragma unroll
-    for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], tw_dir<DIR>(tws[k * 32 + lane]));
-#pragma unroll
-    for (int k = 0; k < 16; ++k) wr[k * kWarpPitch + lane] = v[k];
-    __syncwarp();
 #pragma unroll
     for (int a = 0; a < 16; ++a) v[a] = wr[k1 * kWarpPitch + 2 * a + b];
     dft<16, DIR>(v);
@@ -122,8 +119,8 @@ __global__ void __launch_bounds__(kWarpThreads, 2) warp_stage_kernel(StageDesc d
 #pragma unroll
         for (int k = 0; k < 16; ++k) st_data(dst + (k1 + 16 * k + 256 * b) * io.out_n, cscale(v[k], io.scale));
       }
-      if (!row_in && inplace) __syncthreads();  // the next column load fills every warp's region
-      else __syncwarp();                        // this warp's buffer is reused by the next tile
+      if (!row_in) __syncthreads();  // the next column-side tile writes every warp's region
+      else __syncwarp();             // this warp's buffer is reused by the next tile
     } else {
       __syncwarp();  // every lane has read the transpose buffer
 #pragma unroll
