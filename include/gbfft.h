@@ -174,8 +174,8 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
  * *persistent 0/1, *tma_mask bit s (0-7) = stage s uses the tensor-copy
  * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch, bits
  * 16-19 = CTAs per plane cluster of those launches (2, 4, 8; 0 = by plane
- * size), bit 20 + s = stage s runs the warp-per-pencil kernel (length 512,
- * complex, FP32), *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
+ * size), bit 20 + s = stage s runs the warp-per-pencil kernel (lengths 512
+ * and 256 complex, and the length-256 real x stages; FP32), *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
  * staged candidates. Any output pointer may be NULL.
  */
 int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask, float* ms,

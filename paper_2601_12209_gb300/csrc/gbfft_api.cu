@@ -562,14 +562,18 @@ static const PersistentKernel* find_persistent(const Pipeline& P) {
 }
 
 // Internal launch flag: run the stage with the warp-per-pencil kernel where one
-// is built (length 512, complex, FP32).
+// is built (lengths 512 and 256 complex, the length-256 real x stages; FP32).
 constexpr unsigned kUseWarpKernel = 1u << 30;
 
 static const WarpKernel* find_warp(const StageDesc& d) {
-  if (d.kind != kPlain || d.prec != kPrecFP32 || !d.twn) return nullptr;
+  if (d.prec != kPrecFP32 || !d.twn) return nullptr;
+  if (d.kind != kPlain && d.kind != kR2CPost && d.kind != kC2RPre) return nullptr;
+  if (d.kind == kR2CPost && d.in_mode != kRow) return nullptr;   // the split reads row-side pairs
+  if (d.kind == kC2RPre && d.out_mode != kRow) return nullptr;   // the merge writes row-side pairs
+  if ((d.kind == kR2CPost || d.kind == kC2RPre) && !d.tw2) return nullptr;
   ensure_registry();
   for (const auto& k : warp_registry())
-    if (k.L == d.L && k.dir == d.dir) return &k;
+    if (k.L == d.L && k.dir == d.dir && k.kind == d.kind) return &k;
   return nullptr;
 }
 

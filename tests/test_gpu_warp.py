@@ -1,0 +1,88 @@
+"""Warp-per-pencil stage kernels (L = R1 x 32 in registers, a per-warp transpose and
+lane shuffles; lengths 512 and 256, and the length-256 R2C split / C2R merge x stages):
+every stage position (row/column input and output, in place in the slab schedule)
+against the FP64 oracle, pinned through the tuning bits."""
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_12209_gb300 import _build
+    _build.build()
+    import paper_2601_12209_gb300 as gbmod
+    return gbmod
+
+
+def _pin_warp(plan, pipes=(0, 1)):
+    from paper_2601_12209_gb300 import abi
+    for k in pipes:
+        abi.gbfft_plan_set_tuning(plan.handle, k, False, 0xFF << 20)  # every eligible stage: warp kernel
+
+
+@pytest.mark.parametrize("shape,slab,batch", [((512, 24, 20), False, 1), ((24, 512, 20), False, 2),
+                                              ((20, 24, 512), False, 1), ((512, 512, 4), True, 1),
+                                              ((48, 512, 512), False, 1), ((256, 40, 24), False, 1),
+                                              ((24, 256, 40), False, 2), ((40, 24, 256), False, 1),
+                                              ((256, 256, 6), True, 1)])
+def test_warp512_c2c(gb, shape, slab, batch):
+    nx, ny, nz = shape
+    x = synth.uniform_complex((batch, nz, ny, nx), seed=60 + nx + ny)
+    p = gb.Plan(nx, ny, nz, batch=batch, slab=slab)
+    _pin_warp(p)
+    y = p.forward(x.cuda())
+    z = p.inverse(y)
+    a = p.adjoint(x.cuda())
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    e = oracle.rel_l2(y.cpu().numpy(), oracle.fft3(x.numpy()))
+    e_rt = oracle.rel_l2(z.cpu().numpy(), x.numpy())
+    e_adj = oracle.rel_l2(a.cpu().numpy(), oracle.c2c_adjoint(x.numpy()))
+    print(f"[warp] {shape} slab={slab} batch={batch}: fwd {e:.3e}, round trip {e_rt:.3e}, adjoint {e_adj:.3e}")
+    assert e < TOL and e_rt < TOL and e_adj < TOL
+
+
+def test_warp512_r2c_512_cube(gb):
+    """The 512^3 R2C configuration with the y and z stages on the warp kernel."""
+    n = 512
+    r = synth.normal_real((n, n, n), seed=2)
+    p = gb.Plan(n, n, n, kind="r2c", staged=True)
+    _pin_warp(p)
+    s = p.forward(r.cuda())
+    back = p.inverse(s)
+    torch.cuda.synchronize()
+    e = oracle.rel_l2(s.cpu().numpy(), oracle.rfft3(r.numpy()))
+    e_rt = oracle.rel_l2(back.cpu().numpy(), r.numpy())
+    print(f"[warp] r2c 512^3: fwd {e:.3e}, round trip {e_rt:.3e}")
+    assert e < TOL and e_rt < TOL
+
+
+@pytest.mark.parametrize("shape,slab", [((512, 48, 40), False), ((512, 40, 24), True), ((512, 256, 16), False)])
+def test_warp_r2c_x_stage(gb, shape, slab):
+    """The length-256 real x stages (R2C split after, C2R merge before the transform),
+    with the Poisson pipeline and the adjoints that scale the interior bins."""
+    nx, ny, nz = shape
+    r = synth.normal_real((nz, ny, nx), seed=70 + ny)
+    p = gb.Plan(nx, ny, nz, kind="r2c", slab=slab)
+    _pin_warp(p, pipes=(0, 1, 2))
+    s = p.forward(r.cuda())
+    back = p.inverse(s)
+    adj = p.adjoint(s)
+    phi = p.poisson(r.cuda())
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    e = oracle.rel_l2(s.cpu().numpy(), oracle.rfft3(r.numpy()))
+    e_rt = oracle.rel_l2(back.cpu().numpy(), r.numpy())
+    e_adj = oracle.rel_l2(adj.cpu().numpy(), oracle.r2c_adjoint(s.cpu().numpy().astype("complex128"), nx))
+    e_p = oracle.rel_l2(phi.cpu().numpy(), oracle.poisson(r.numpy()))
+    print(f"[warp] r2c {shape} slab={slab}: fwd {e:.3e}, round trip {e_rt:.3e}, adjoint {e_adj:.3e}, poisson {e_p:.3e}")
+    assert e < TOL and e_rt < TOL and e_adj < TOL and e_p < TOL
