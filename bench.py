@@ -263,7 +263,7 @@ def main():
                     help="run one 512^3 case for a profiler and exit: staged_r2c, staged_lsu_r2c, persistent_r2c, "
                          "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024, "
                          "split_bf16_1024, split_fp32_1024 (C2C 1024x512x64, staged thread-load launches; "
-                         "tensor-core radix-16 passes unless fp32)")
+                         "tensor-core radix-16 passes unless fp32); or pinned_r2c:<fwd bits>:<inv bits>")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -446,6 +446,15 @@ def ncu_case(name):
         plan = gb.Plan(1024, 512, 64, precision=prec if prec == "fp32" else prec + "_split", staged=True, tma=False)
         x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
         kind = "c2c"
+    elif name.startswith("pinned_r2c"):
+        # pinned_r2c:<forward bits>:<inverse bits>: R2C 512^3 with a fixed launch choice (the tuning bits of
+        # gbfft_plan_set_tuning), e.g. the benchmark's autotuned choice, so a profile sees the timed kernels
+        _, fwd, inv = name.split(":")
+        kind = "r2c"
+        plan = gb.Plan(N, N, N, kind=kind)
+        abi.gbfft_plan_set_tuning(plan.handle, 0, False, int(fwd, 0))
+        abi.gbfft_plan_set_tuning(plan.handle, 1, False, int(inv, 0))
+        x = synth.normal_real((N, N, N), seed=2).cuda()
     else:
         kind = "r2c" if name.endswith("r2c") else "c2c"
         plan = gb.Plan(N, N, N, kind=kind, staged=name.startswith("staged"), slab=name.startswith("slab"),
