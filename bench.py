@@ -72,8 +72,8 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# the sources of the stage and tensor-copy kernels' device code
-KERNEL_SOURCES = ("gbfft_internal.h", "gbfft_device.cuh", "gbfft_kernels.cuh", "gbfft_tma.cuh")
+# the sources of the stage, tensor-copy and warp-per-pencil kernels' device code
+KERNEL_SOURCES = ("gbfft_internal.h", "gbfft_device.cuh", "gbfft_kernels.cuh", "gbfft_tma.cuh", "gbfft_warp.cuh")
 # ... and of the fused plane kernels
 PLANE_SOURCES = KERNEL_SOURCES + ("gbfft_plane.cuh",)
 
