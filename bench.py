@@ -106,6 +106,39 @@ def ncu_traffic(kernel_key):
         return None
 
 
+def _parse_cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def bind_near_gpu(torch, device_index):
+    """Run this process on the CPUs of the NUMA node the GPU is attached to (from sysfs), so that
+    pinned host buffers allocated afterwards sit next to the GPU's link. Returns the node or None."""
+    try:
+        uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+        ident = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        bus = subprocess.run(["nvidia-smi", f"--id={ident}", "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        with open(f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest.lower()}/numa_node") as fh:
+            node = int(fh.read().strip())
+        if node < 0:
+            return None
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as fh:
+            local = _parse_cpulist(fh.read()) & os.sched_getaffinity(0)
+        if local:
+            os.sched_setaffinity(0, local)
+        return node
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -376,7 +409,8 @@ def main():
     traffic = ncu_traffic(dom[0])
     launches_per_step = sum(1 if t["persistent"] else 3 for t in (tuning["forward"], tuning["inverse"]))
 
-    # end to end through the C ABI on pinned host buffers
+    # end to end through the C ABI on pinned host buffers, allocated on the GPU's NUMA node
+    numa_node = bind_near_gpu(torch, dev.index if dev.index is not None else 0)
     h_in = synth.normal_real((N, N, N), seed=2).pin_memory()
     h_spec = torch.empty((N, N, N // 2 + 1), dtype=torch.complex64).pin_memory()
     h_out = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
@@ -417,7 +451,8 @@ def main():
         "tuning": {k: {"persistent": v["persistent"], "tma_mask": v["tma_mask"], "ms": v["ms"]}
                    for k, v in tuning.items()},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3, "path": "gbfft_exec_host (pinned host buffers)"},
+                "ms_per_step": e2e_s * 1e3, "path": "gbfft_exec_host (pinned host buffers)",
+                "host_numa_node": numa_node},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "device_error": err,
