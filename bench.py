@@ -567,6 +567,17 @@ def poisson_variant(torch, gb, abi, stream, steps, warmup):
     nc = (n // 2 + 1) * n * n
     alg = 2 * (4 * n ** 3 + 8 * nc) + 2 * 16 * nc + 16 * nc  # x, y out and back; fused z: one read + one write
     out = {"ms": ms, "alg_gbs": alg / (ms * 1e-3) / 1e9, "tuning": tune["poisson"]}
+    # (Periodic, Periodic, Bounded): the same pipeline with the DCT z stage
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            p.poisson(f, phi, stream=stream, bounded=True)
+        e0.record(stream)
+        for _ in range(steps):
+            p.poisson(f, phi, stream=stream, bounded=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    msb = e0.elapsed_time(e1) / steps
+    out["bounded_z"] = {"ms": msb, "alg_gbs": alg / (msb * 1e-3) / 1e9}
     p.close()
     return out
 

@@ -146,10 +146,24 @@ int gbfft_exec_inverse_adjoint(gbfft_plan plan, const void* in, void* out, void*
 int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream);
 
 /*
+ * Poisson solve on the (Periodic, Periodic, Bounded) topology (Section VI-B):
+ * x and y periodic as in gbfft_exec_poisson; z bounded by walls with a zero
+ * normal derivative (Neumann), the nz values at cell centres of a box of
+ * height pi. Along z the solve expands in cosines: DCT-II (real-to-real,
+ * Section V-B) forward and DCT-III back, each computed as one length-nz
+ * complex FFT, fused into the z stage with the multiplier
+ * m(k) = -1/(kx^2 + ky^2 + kz^2) (kz = cosine index 0..nz-1), m(0) = 0, and
+ * the normalisation 1/(2 nx ny nz). R2C plans only; in and out are real
+ * [batch][nz][ny][nx]. The operator is symmetric: this call is its own adjoint.
+ */
+int gbfft_exec_poisson_bounded(gbfft_plan plan, const void* in, void* out, void* stream);
+
+/*
  * End-to-end call on HOST buffers: copies `host_in` to the device, runs
  * `op`, copies the result to `host_out`, and waits for completion. Uses
  * plan-owned device buffers (allocated on first use). Pinned host memory
- * gives asynchronous copies. op may also be 4 for gbfft_exec_poisson.
+ * gives asynchronous copies. op may also be 4 for gbfft_exec_poisson, 5 for
+ * gbfft_exec_poisson_bounded.
  */
 int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out);
 

@@ -250,6 +250,68 @@ def poisson(f, threads: int | None = None) -> np.ndarray:
     return irfft3(F, nx, threads=threads)
 
 
+# ------------------------------------------------- bounded z: real-to-real DCT
+# Section V-B lists real-to-real transforms (DCT, DST); Section VI-B solves the
+# Poisson equation on the (Periodic, Periodic, Bounded) topology. Reading: the
+# bounded axis z holds nz cell centres z_n = (n + 1/2) pi / nz of a box of
+# height pi between walls with zero normal derivative (Neumann), so the
+# cosines cos(k z_n), k = 0..nz-1, diagonalise the Laplacian with eigenvalue
+# -k^2 -- integer wavenumbers, like the periodic axes of length 2 pi.
+
+def _cos_matrix(n: int) -> np.ndarray:
+    """C[k, m] = cos(pi k (2m + 1) / 2n), from the integer argument reduced mod 4n."""
+    k = np.arange(n)[:, None]
+    m = np.arange(n)[None, :]
+    t = (k * (2 * m + 1)) % (4 * n)
+    return np.cos(2.0 * np.pi * t / (4.0 * n))
+
+
+def dct2_z(x) -> np.ndarray:
+    """DCT-II (REDFT10) along z (axis -3): Y_k = 2 sum_n x_n cos(pi k (2n + 1) / 2 nz)."""
+    a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x)
+    a = a.astype(np.complex128 if np.iscomplexobj(a) else np.float64)
+    C = _cos_matrix(a.shape[-3])
+    return 2.0 * np.einsum("kn,...nyx->...kyx", C, a)
+
+
+def dct3_z(y) -> np.ndarray:
+    """DCT-III (REDFT01) along z: x_n = Y_0 + 2 sum_{k>0} Y_k cos(pi k (2n + 1) / 2 nz); dct3(dct2(x)) = 2 nz x."""
+    a = np.asarray(y.detach().cpu().numpy() if hasattr(y, "detach") else y)
+    a = a.astype(np.complex128 if np.iscomplexobj(a) else np.float64)
+    n = a.shape[-3]
+    w = np.full(n, 2.0)
+    w[0] = 1.0
+    C = _cos_matrix(n)
+    return np.einsum("kn,...kyx->...nyx", C * w[:, None], a)
+
+
+def poisson_bounded_multiplier(nx: int, ny: int, nz: int) -> np.ndarray:
+    """m = -1/(kx^2 + ky^2 + kz^2) on [nz][ny][nx] with kx, ky periodic integers and kz = 0..nz-1; m(0) = 0."""
+    kx = wavenumbers(nx)
+    ky = wavenumbers(ny)
+    kz = np.arange(nz, dtype=np.float64)
+    k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    m = np.zeros_like(k2)
+    m[k2 > 0] = -1.0 / k2[k2 > 0]
+    return m
+
+
+def poisson_bounded(f, threads: int | None = None) -> np.ndarray:
+    """(P,P,Bounded) Poisson solve: phi = DCT3_z(F_xy^-1(m * F_xy(DCT2_z(f)))) / (2 nx ny nz).
+
+    F_xy is the 2D DFT of every z-plane (the separable 3D oracle on planes of
+    depth 1); the mean (k = 0) mode is set to zero.
+    """
+    r = _as_f64(f)
+    nz, ny, nx = r.shape[-3:]
+    lead = r.shape[:-3]
+    Y = dct2_z(r).reshape((-1, 1, ny, nx))       # z-planes as a batch of depth-1 grids
+    S = fft3(Y.astype(np.complex128), threads=threads).reshape(lead + (nz, ny, nx))
+    S *= poisson_bounded_multiplier(nx, ny, nz)
+    T = fft3(S.reshape((-1, 1, ny, nx)), sign=+1, threads=threads).reshape(lead + (nz, ny, nx))
+    return np.ascontiguousarray(dct3_z(T).real / (2.0 * nx * ny * nz))
+
+
 # ---------------------------------------------------------------- stage layouts
 # Algorithm 1 keeps three arrays, each with its transform axis complete and
 # contiguous. Concretely (a reading: the paper leaves the order of the other

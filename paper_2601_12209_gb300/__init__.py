@@ -130,10 +130,20 @@ class Plan:
     def inverse_adjoint(self, x, out=None, stream=None):
         return self.exec(GBFFT_OP_INVERSE_ADJOINT, x, out, stream)
 
-    def poisson(self, f, out=None, stream=None):
+    def poisson(self, f, out=None, stream=None, bounded: bool = False):
+        """Periodic Poisson solve; bounded=True: z bounded by Neumann walls (cosine expansion)."""
         if self.kind != "r2c":
             raise ValueError("poisson needs an r2c plan")
-        return self.exec(abi.GBFFT_OP_POISSON, f, out, stream)
+        if not bounded:
+            return self.exec(abi.GBFFT_OP_POISSON, f, out, stream)
+        idt, ishape, odt, oshape = self._io(abi.GBFFT_OP_POISSON)
+        _check_tensor(f, idt, ishape, "input")
+        if out is None:
+            out = torch.empty_like(f)
+        else:
+            _check_tensor(out, odt, oshape, "out")
+        abi.gbfft_exec_poisson_bounded(self.handle, f.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
 
     def exec_host(self, op: int, host_in: torch.Tensor, host_out: torch.Tensor) -> torch.Tensor:
         """End-to-end on host tensors (pinned recommended): H2D copy, op, D2H copy, wait."""

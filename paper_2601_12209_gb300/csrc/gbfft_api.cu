@@ -261,6 +261,7 @@ struct gbfft_plan_s {
   // twiddle tables (device)
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr, *tw2 = nullptr;
   float2 *twn_x = nullptr, *twn_y = nullptr, *twn_z = nullptr;  // natural W_L^m tables per axis
+  float2* tw4_z = nullptr;  // W_4nz^k, k <= nz: bounded-z (DCT) Poisson stage (R2C plans)
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -469,16 +470,21 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       add(Y, r2c ? 2 : 1, r2c ? 2 : 1);
       add(X, r2c ? 2 : 1, 1);
     }
-  } else {  // Poisson (R2C plans)
+  } else {  // Poisson (R2C plans); op 5: bounded z (Neumann walls, DCT-II / DCT-III along z)
     const int M = Lx;
+    const bool bounded = op == 5;
+    // DCT-III(DCT-II(x)) = 2 nz x; the x,y transforms contribute nx ny
+    const float invNb = (float)(1.0 / (2.0 * (double)nx * (double)ny * (double)nz));
     if (!is_slab(p)) {
       StageDesc X = mk(in, W1, M, kR2CPost, -1, B, nz, ny, NA, (long long)M * ny, M, 1, kRow, Nc,
                        (long long)nxc * ny, 1, ny, kCol, 1.f, 1.f, p->tw_x, p->tw2);
       StageDesc Y = mk(W1, W2, ny, kPlain, -1, B, nxc, nz, Nc, ny, (long long)nxc * ny, 1, kRow, Nc,
                        (long long)ny * nz, 1, nz, kCol, 1.f, 1.f, p->tw_y, nullptr);
       dep(Y, kDepGroup, X);
-      StageDesc PZ = mk(W2, W2, nz, kPoissonZ, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nz,
-                        (long long)ny * nz, 1, kRow, invN, 1.f, p->tw_z, nullptr);
+      StageDesc PZ = bounded ? mk(W2, W2, nz, kPoissonZB, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc,
+                                  nz, (long long)ny * nz, 1, kRow, invNb, 1.f, p->tw_z, p->tw4_z)
+                             : mk(W2, W2, nz, kPoissonZ, -1, B, ny, nxc, Nc, nz, (long long)ny * nz, 1, kRow, Nc, nz,
+                                  (long long)ny * nz, 1, kRow, invN, 1.f, p->tw_z, nullptr);
       PZ.pz_nx = nx;
       PZ.pz_ny = ny;
       dep(PZ, kDepGroup, Y);
@@ -499,8 +505,9 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       StageDesc Y = mk(W1, W1, ny, kPlain, -1, B, nz, nxc, Nc, (long long)nxc * ny, 1, nxc, kCol, Nc,
                        (long long)nxc * ny, 1, nxc, kCol, 1.f, 1.f, p->tw_y, nullptr);
       dep(Y, kDepOuter, X);
-      StageDesc PZ = mk(W1, W1, nz, kPoissonZ, -1, B, ny, nxc, Nc, nxc, 1, (long long)nxc * ny, kCol, Nc, nxc,
-                        1, (long long)nxc * ny, kCol, invN, 1.f, p->tw_z, nullptr);
+      StageDesc PZ = mk(W1, W1, nz, bounded ? kPoissonZB : kPoissonZ, -1, B, ny, nxc, Nc, nxc, 1,
+                        (long long)nxc * ny, kCol, Nc, nxc, 1, (long long)nxc * ny, kCol, bounded ? invNb : invN, 1.f,
+                        p->tw_z, bounded ? p->tw4_z : nullptr);
       PZ.pz_nx = nx;
       PZ.pz_ny = ny;
       dep(PZ, kDepSameGchunk, Y);
@@ -894,6 +901,7 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->twn_x);
   cudaFree(p->twn_y);
   cudaFree(p->twn_z);
+  cudaFree(p->tw4_z);
   if (p->h_stream) cudaStreamDestroy(p->h_stream);
   for (auto& c : p->timed)
     for (int k = 0; k < c.nev; ++k) cudaEventDestroy(c.ev[k]);
@@ -1023,7 +1031,8 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   bool ok = p->tw_x && p->tw_y && p->tw_z && p->twn_x && p->twn_y && p->twn_z;
   if (ok && kind == GBFFT_R2C) {
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
-    ok = p->tw2 != nullptr;
+    p->tw4_z = upload_table(twiddle_table(4 * nz, nz + 1));
+    ok = p->tw2 != nullptr && p->tw4_z != nullptr;
   }
   // persistent-launch counters: sized for the largest pipeline
   size_t words = 0;
@@ -1100,26 +1109,39 @@ int gbfft_exec_inverse_adjoint(gbfft_plan plan, const void* in, void* out, void*
   return gbfft_exec(plan, GBFFT_OP_INVERSE_ADJOINT, in, out, stream);
 }
 
-int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream) {
+}  // extern "C"
+
+// op 4: periodic z; op 5: bounded z (DCT)
+static int exec_poisson_op(gbfft_plan plan, int op, const void* in, void* out, void* stream) {
   if (!plan) return GBFFT_ERR_INVALID_ARG;
   if (plan->kind != GBFFT_R2C || plan->batch < 1) return GBFFT_ERR_INVALID_ARG;
-  if (!find_stage(plan->nz, -1, kPoissonZ)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  if (!find_stage(plan->nz, -1, op == 5 ? kPoissonZB : kPoissonZ)) return GBFFT_ERR_UNSUPPORTED_SIZE;
   int rc = check_ptrs(in, out);
   if (rc) return rc;
   if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
   rc = ensure_workspace(plan);
   if (rc) return rc;
-  Buf bin{const_cast<void*>(in), (long long)(op_in_bytes(plan, 4) / sizeof(float2))};
-  Buf bout{out, (long long)(op_out_bytes(plan, 4) / sizeof(float2))};
-  Pipeline P = build_pipeline(plan, kPipePoisson, 4, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
+  Buf bin{const_cast<void*>(in), (long long)(op_in_bytes(plan, op) / sizeof(float2))};
+  Buf bout{out, (long long)(op_out_bytes(plan, op) / sizeof(float2))};
+  Pipeline P = build_pipeline(plan, kPipePoisson, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
   return run_pipeline(plan, P, kPipePoisson, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" {
+
+int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream) {
+  return exec_poisson_op(plan, 4, in, out, stream);
+}
+
+int gbfft_exec_poisson_bounded(gbfft_plan plan, const void* in, void* out, void* stream) {
+  return exec_poisson_op(plan, 5, in, out, stream);
 }
 
 static size_t op_in_bytes(const gbfft_plan_s* p, int op) {
   const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);  // rowA complex per row
   const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
   if (p->kind == GBFFT_C2C) return spec_b;
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4) return real_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4 || op == 5) return real_b;
   return spec_b;
 }
 
@@ -1133,7 +1155,7 @@ static size_t op_out_bytes(const gbfft_plan_s* p, int op) {
 
 int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out) {
   if (!plan || !host_in || !host_out) return GBFFT_ERR_INVALID_ARG;
-  if (op < 0 || op > 4) return GBFFT_ERR_INVALID_ARG;
+  if (op < 0 || op > 5) return GBFFT_ERR_INVALID_ARG;
   if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
   const size_t ib = op_in_bytes(plan, op), ob = op_out_bytes(plan, op);
   if (!plan->h_stream && cudaStreamCreateWithFlags(&plan->h_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -1149,7 +1171,8 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
   cudaStream_t s = plan->h_stream;
   if (cudaMemcpyAsync(plan->h_in_dev, host_in, ib, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return GBFFT_ERR_CUDA;
-  int rc = op == 4 ? gbfft_exec_poisson(plan, plan->h_in_dev, plan->h_out_dev, s)
+  int rc = op == 5   ? gbfft_exec_poisson_bounded(plan, plan->h_in_dev, plan->h_out_dev, s)
+           : op == 4 ? gbfft_exec_poisson(plan, plan->h_in_dev, plan->h_out_dev, s)
                    : gbfft_exec(plan, op, plan->h_in_dev, plan->h_out_dev, s);
   if (rc) return rc;
   if (cudaMemcpyAsync(host_out, plan->h_out_dev, ob, cudaMemcpyDeviceToHost, s) != cudaSuccess)

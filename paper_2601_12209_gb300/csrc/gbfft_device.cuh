@@ -799,6 +799,64 @@ __device__ __forceinline__ void poisson_multiply(float2* sm, int gfirst, int ky_
   __syncthreads();
 }
 
+// ------------------------------------------ bounded z: DCT-II / DCT-III by FFT
+//
+// Along a bounded axis with Neumann walls (cell centres z_n = (n + 1/2) dz)
+// the Poisson solve expands in cosines: DCT-II (FFTW's REDFT10)
+//   Y_k = 2 sum_n x_n cos(pi k (2n + 1) / 2L),
+// and back with DCT-III (REDFT01) x_n = Y_0 + 2 sum_{k>0} Y_k cos(pi k (2n + 1) / 2L),
+// which returns 2L x. Both run as one length-L complex FFT each (the
+// reordering v_m = x_2m, v_(L-1-m) = x_(2m+1) of Makhoul's method): with
+// V = FFT(v) and V_c[k] = conj V[(L - k) mod L], the real and imaginary parts
+// of x transform separately, Vr = (V + V_c) / 2, Vi = (V - V_c) / 2i, and
+//   Y_k = 2 Re(W_k Vr_k) + 2 i Re(W_k Vi_k),  W_k = exp(-i pi k / 2L);
+// backwards V'_k = conj(W_k) (Yr_k - i Yr_(L-k)) + i conj(W_k) (Yi_k - i Yi_(L-k))
+// (Y_L = 0) and the unscaled inverse FFT of V' is v.
+
+// position of element i of a pencil in the reordered sequence v
+__device__ __forceinline__ int dct_pos(int i, int L) { return (i & 1) ? L - 1 - (i >> 1) : (i >> 1); }
+
+// DCT-II of every pencil's FFT (rows 0..L-1), multiply by the bounded Poisson
+// symbol, and prepare the DCT-III FFT input, pair (k, L - k) per item. The
+// symbol is -inv_n / (kx^2 + ky^2 + kz^2) with kz = k (cosine index), kx the
+// pencil's half-spectrum bin, ky the outer index folded to [-ny/2, ny/2].
+template <int L, int THREADS>
+__device__ __forceinline__ void dct_poisson_bounded(float2* sm, const float2* w4, int gfirst, int ky_idx, int ny,
+                                                    float inv_n) {
+  constexpr int NPAIR = L / 2 + 1;
+  const float ky = (float)(ky_idx <= ny / 2 ? ky_idx : ky_idx - ny);
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    const int j = k == 0 ? 0 : L - k;
+    if (k > j) continue;  // the pair was taken by item (j, k)
+    const float kx = (float)(gfirst + p);
+    const float2 A = sm[swz(k, p)], B = sm[swz(j, p)];
+    const float2 Wk = w4[k], Wj = w4[j];
+    auto forward = [](float2 a, float2 b, float2 w) {
+      // Vr = (a + conj b) / 2, Vi = (a - conj b) / 2i; Y = 2 Re(w Vr) + 2 i Re(w Vi)
+      const float2 vr = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+      const float2 vi = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+      return make_float2(2.f * (w.x * vr.x - w.y * vr.y), 2.f * (w.x * vi.x - w.y * vi.y));
+    };
+    float2 Yk = forward(A, B, Wk);
+    float2 Yj = forward(B, A, Wj);
+    const float kz_k = (float)k, kz_j = (float)j;
+    const float k2k = kx * kx + ky * ky + kz_k * kz_k, k2j = kx * kx + ky * ky + kz_j * kz_j;
+    Yk = cscale(Yk, k2k > 0.f ? -inv_n / k2k : 0.f);
+    Yj = cscale(Yj, k2j > 0.f ? -inv_n / k2j : 0.f);
+    if (k == 0) {
+      sm[swz(0, p)] = Yk;  // Y_L = 0 and W_0 = 1: V'_0 = Y_0
+    } else {
+      // V'_k = conj(Wk) (Yr_k - i Yr_j) + i conj(Wk) (Yi_k - i Yi_j) = conj(Wk) (Yr_k + Yi_j + i (Yi_k - Yr_j))
+      const float2 uk = make_float2(Yk.x + Yj.y, Yk.y - Yj.x);
+      const float2 uj = make_float2(Yj.x + Yk.y, Yj.y - Yk.x);
+      sm[swz(k, p)] = cmul(cconj(Wk), uk);
+      if (j != k) sm[swz(j, p)] = cmul(cconj(Wj), uj);
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------- tile driver
 
 template <int L, int DIR, int KIND>
@@ -884,6 +942,37 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
     c2r_pre<L, THREADS>(sm, tw2, d.interior);
     fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io);
     row_store<THREADS, L>(sm, io);
+  } else if constexpr (KIND == kPoissonZB) {
+    // bounded z pencils: reorder into v, FFT, DCT-II + multiply + DCT-III input, FFT, reorder back
+    TileIO io_nos = io;
+    io_nos.scale = 1.f;
+    for (int it = threadIdx.x; it < L * 16; it += THREADS) {
+      int p, n;
+      if (row_in) {  // lanes along the row
+        n = it % L;
+        p = it / L;
+      } else {  // lanes along the pencils
+        p = it & 15;
+        n = it >> 4;
+      }
+      const float2 a = (p < io.valid) ? ld_data(io.gin + p * io.in_g + n * io.in_n) : make_float2(0.f, 0.f);
+      sm[swz(dct_pos(n, L), p)] = a;
+    }
+    __syncthreads();
+    fft_passes<L, -1, THREADS, false, false, false>(sm, tw, io_nos);
+    dct_poisson_bounded<L, THREADS>(sm, tw2, g0, o, d.pz_ny, d.scale);
+    fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io_nos);
+    for (int it = threadIdx.x; it < L * 16; it += THREADS) {
+      int p, n;
+      if (row_out) {
+        n = it % L;
+        p = it / L;
+      } else {
+        p = it & 15;
+        n = it >> 4;
+      }
+      if (p < io.valid) st_data(io.gout + p * io.out_g + n * io.out_n, sm[swz(dct_pos(n, L), p)]);
+    }
   } else if constexpr (KIND == kPoissonZ) {
     // z pencils of the half spectrum: forward, multiply, inverse, in one tile
     TileIO io_nos = io;

@@ -22,6 +22,7 @@ enum TileKind : int {
   kC2RPre = 2,    // merge L+1 half-spectrum bins into L complex, then FFT
   kIdentity = 3,  // no arithmetic: pure pack/transpose/unpack (debug, bit-exact tests)
   kPoissonZ = 4,  // forward FFT, multiply by -1/|k|^2, inverse FFT (fused Poisson z stage)
+  kPoissonZB = 5, // bounded z: DCT-II, multiply by -1/|k|^2, DCT-III (fused Poisson z stage, Neumann walls)
 };
 
 // Arithmetic of a stage's radix-16 passes: FP32 on the CUDA cores, or dense
@@ -68,7 +69,7 @@ struct StageDesc {
   float scale;     // multiplies every output value
   float interior;  // R2C/C2R: multiplies bins 1..L-1 of the half spectrum
   const float2* tw;    // packed per-pass twiddles of length L (tw_table_len(L) entries, device)
-  const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R only)
+  const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R); W_4L^k, k < L (bounded Poisson z)
   int tw_len;          // entries of tw
   const float2* twn;   // natural twiddles W_L^m = exp(-2 pi i m / L), m in [0, L) (device)
   // Poisson z stage: wavenumber bookkeeping of the tile's pencils

@@ -8,7 +8,8 @@ namespace gbfft {
   v.push_back(make_stage_entry<L, -1, kPlain>());        \
   v.push_back(make_stage_entry<L, 1, kPlain>());         \
   v.push_back(make_stage_entry<L, -1, kIdentity>());     \
-  v.push_back(make_stage_entry<L, -1, kPoissonZ>());
+  v.push_back(make_stage_entry<L, -1, kPoissonZ>());        \
+  v.push_back(make_stage_entry<L, -1, kPoissonZB>());
 #define GBFFT_STAGE_REAL(L)                              \
   v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
   v.push_back(make_stage_entry<L, 1, kC2RPre>());

@@ -320,3 +320,35 @@ def test_plane_waves_closed_form():
     assert torch.equal(u, synth.uniform_complex_slabs((9, 5, 4), seed=3, planes=4))
     r = torch.view_as_real(u)
     assert float(r.abs().max()) <= 1.0 and u.dtype == torch.complex64
+
+
+def test_dct_z_against_library_and_inverse():
+    """DCT-II / DCT-III along z: against scipy.fft.dct (an independent library), the
+    inverse pair identity, and a cosine basis vector (closed form N at its own bin)."""
+    sf = pytest.importorskip("scipy.fft")
+    x = synth.normal_real((2, 9, 5, 4), seed=31).numpy().astype(np.float64)
+    np.testing.assert_allclose(oracle.dct2_z(x), sf.dct(x, type=2, axis=-3), atol=1e-12)
+    np.testing.assert_allclose(oracle.dct3_z(x), sf.dct(x, type=3, axis=-3), atol=1e-12)
+    np.testing.assert_allclose(oracle.dct3_z(oracle.dct2_z(x)), 2 * 9 * x, atol=1e-12)
+    n, k0 = 12, 5
+    e = np.cos(np.pi * k0 * (2 * np.arange(n) + 1) / (2 * n))[:, None, None]
+    y = oracle.dct2_z(e)[:, 0, 0]
+    ref = np.zeros(n)
+    ref[k0] = n
+    np.testing.assert_allclose(y, ref, atol=1e-12)
+
+
+def test_poisson_bounded_single_mode_and_symmetry():
+    """(P,P,Bounded): a single cosine-in-z, Fourier-in-xy mode solves to -f/|k|^2 exactly;
+    the operator is symmetric; the mean mode is removed."""
+    nx, ny, nz = 16, 12, 10
+    i, j, n = np.arange(nx), np.arange(ny), np.arange(nz)
+    for kx, ky, kz in [(3, -2, 4), (0, 5, 1), (8, 0, 9), (1, 1, 0)]:
+        f = (np.cos(kz * (n + 0.5) * np.pi / nz)[:, None, None]
+             * np.cos(kx * 2 * np.pi * i / nx + ky * 2 * np.pi * j[:, None] / ny)[None, :, :])
+        np.testing.assert_allclose(oracle.poisson_bounded(f), -f / (kx * kx + ky * ky + kz * kz), atol=1e-13)
+    a = synth.normal_real((nz, ny, nx), seed=32).numpy().astype(np.float64)
+    b = synth.normal_real((nz, ny, nx), seed=33).numpy().astype(np.float64)
+    np.testing.assert_allclose(np.sum(oracle.poisson_bounded(a) * b), np.sum(a * oracle.poisson_bounded(b)),
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle.poisson_bounded(np.ones((nz, ny, nx))), 0.0, atol=1e-14)
