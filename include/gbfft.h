@@ -158,6 +158,26 @@ int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream)
  */
 int gbfft_exec_poisson_bounded(gbfft_plan plan, const void* in, void* out, void* stream);
 
+/* real-to-real kinds along z (Section V-B: R2R transforms, DCT and DST) */
+#define GBFFT_R2R_DCT 0 /* forward DCT-II (FFTW REDFT10), inverse DCT-III (REDFT01) */
+#define GBFFT_R2R_DST 1 /* forward DST-II (RODFT10), inverse DST-III (RODFT01) */
+
+/*
+ * Real-to-real transform along z with Fourier transforms along x and y (the
+ * spectral basis of the (Periodic, Periodic, Bounded) topology): forward
+ * (inverse = 0) takes the plan's forward input (real [b][nz][ny][nx] for R2C
+ * plans, complex for C2C) to a complex [b][nz][ny][nxc] array whose z index is
+ * the cosine (DCT) or sine (DST) index k of
+ *   DCT-II: Y_k = 2 sum_n x_n cos(pi k (2n + 1) / 2nz)
+ *   DST-II: Y_k = 2 sum_n x_n sin(pi (k + 1) (2n + 1) / 2nz)
+ * (unnormalised, x and y as gbfft_exec_forward); inverse = 1 applies DCT-III /
+ * DST-III along z and the inverse x, y transforms, scaled by 1 / (2 nx ny nz),
+ * so inverse(forward(x)) = x. Each z transform runs as one length-nz complex
+ * FFT inside the z stage. Pencil or slab plans; the spectrum's layout is
+ * gbfft_exec_forward's (natural, or [b][kx][ky][kz] with GBFFT_TRANSPOSED_OUT).
+ */
+int gbfft_exec_r2r_z(gbfft_plan plan, int r2r, int inverse, const void* in, void* out, void* stream);
+
 /*
  * End-to-end call on HOST buffers: copies `host_in` to the device, runs
  * `op`, copies the result to `host_out`, and waits for completion. Uses

@@ -285,6 +285,55 @@ def dct3_z(y) -> np.ndarray:
     return np.einsum("kn,...kyx->...nyx", C * w[:, None], a)
 
 
+def _sin_matrix(n: int) -> np.ndarray:
+    """S[k, m] = sin(pi (k + 1) (2m + 1) / 2n), from the integer argument reduced mod 4n."""
+    k = np.arange(n)[:, None]
+    m = np.arange(n)[None, :]
+    t = ((k + 1) * (2 * m + 1)) % (4 * n)
+    return np.sin(2.0 * np.pi * t / (4.0 * n))
+
+
+def dst2_z(x) -> np.ndarray:
+    """DST-II (RODFT10) along z: Y_k = 2 sum_n x_n sin(pi (k + 1) (2n + 1) / 2 nz)."""
+    a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x)
+    a = a.astype(np.complex128 if np.iscomplexobj(a) else np.float64)
+    return 2.0 * np.einsum("kn,...nyx->...kyx", _sin_matrix(a.shape[-3]), a)
+
+
+def dst3_z(y) -> np.ndarray:
+    """DST-III (RODFT01) along z: x_n = (-1)^n Y_(nz-1) + 2 sum_{k<nz-1} Y_k sin(pi (k + 1) (2n + 1) / 2 nz)."""
+    a = np.asarray(y.detach().cpu().numpy() if hasattr(y, "detach") else y)
+    a = a.astype(np.complex128 if np.iscomplexobj(a) else np.float64)
+    n = a.shape[-3]
+    w = np.full(n, 2.0)
+    w[-1] = 1.0
+    return np.einsum("kn,...kyx->...nyx", _sin_matrix(n) * w[:, None], a)
+
+
+def r2r_z(x, kind: str = "dct", inverse: bool = False, nx: int | None = None, threads: int | None = None):
+    """Fourier along x (R2C for real input) and y, real-to-real along z (DCT-II / DST-II); inverse:
+    DCT-III / DST-III along z, inverse x and y transforms, scaled by 1 / (2 nx ny nz)."""
+    if not inverse:
+        a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x)
+        lead, (nz, ny, n_x) = a.shape[:-3], a.shape[-3:]
+        planes = a.reshape((-1, 1, ny, n_x))
+        if np.iscomplexobj(a):
+            S = fft3(planes.astype(np.complex128), threads=threads)
+        else:
+            S = rfft3(planes.astype(np.float64), threads=threads)
+        S = S.reshape(lead + (nz, ny, S.shape[-1]))
+        return dct2_z(S) if kind == "dct" else dst2_z(S)
+    a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x).astype(np.complex128)
+    lead, (nz, ny, nk) = a.shape[:-3], a.shape[-3:]
+    T = dct3_z(a) if kind == "dct" else dst3_z(a)
+    planes = T.reshape((-1, 1, ny, nk))
+    if nx is None:  # complex data: full x spectrum
+        out = fft3(planes, sign=+1, threads=threads).reshape(lead + (nz, ny, nk))
+        return out / (2.0 * nk * ny * nz)
+    out = c2r_unscaled(planes, nx, threads=threads).reshape(lead + (nz, ny, nx))
+    return out / (2.0 * nx * ny * nz)
+
+
 def poisson_bounded_multiplier(nx: int, ny: int, nz: int) -> np.ndarray:
     """m = -1/(kx^2 + ky^2 + kz^2) on [nz][ny][nx] with kx, ky periodic integers and kz = 0..nz-1; m(0) = 0."""
     kx = wavenumbers(nx)

@@ -130,6 +130,24 @@ class Plan:
     def inverse_adjoint(self, x, out=None, stream=None):
         return self.exec(GBFFT_OP_INVERSE_ADJOINT, x, out, stream)
 
+    def r2r_z(self, x, kind: str = "dct", inverse: bool = False, out=None, stream=None):
+        """Real-to-real transform along z (kind "dct": DCT-II / DCT-III, "dst": DST-II / DST-III) with
+        Fourier x and y: forward takes the forward op's input to its spectrum shape; inverse undoes it."""
+        if kind not in ("dct", "dst"):
+            raise ValueError("kind must be 'dct' or 'dst'")
+        op = abi.GBFFT_OP_INVERSE if inverse else abi.GBFFT_OP_FORWARD
+        idt, ishape, odt, oshape = self._io(op)
+        _check_tensor(x, idt, ishape, "input")
+        if out is None:
+            out = torch.empty(oshape, dtype=odt, device=x.device)
+            if x.dim() == 3 and self.batch == 1:
+                out = out.view(oshape[1:])
+        else:
+            _check_tensor(out, odt, oshape, "out")
+        abi.gbfft_exec_r2r_z(self.handle, abi.GBFFT_R2R_DCT if kind == "dct" else abi.GBFFT_R2R_DST, inverse,
+                             x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
     def poisson(self, f, out=None, stream=None, bounded: bool = False):
         """Periodic Poisson solve; bounded=True: z bounded by Neumann walls (cosine expansion)."""
         if self.kind != "r2c":

@@ -436,7 +436,8 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
     }
   } else if (pipe == kPipeInv) {
     const float interior = (op == GBFFT_OP_ADJOINT) ? 0.5f : 1.f;
-    const float scale = (op == GBFFT_OP_INVERSE) ? invN : 1.f;
+    // the real-to-real inverses (DCT-III, DST-III) return 2 nz times the input along z
+    const float scale = (op == GBFFT_OP_INVERSE) ? invN : ((op == 7 || op == 9) ? 0.5f * invN : 1.f);
     if (!is_slab(p)) {
       void* Cb = r2c ? W1 : out;
       void* Bb = r2c ? W2 : W1;
@@ -524,6 +525,12 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       add(Xi, 2, 1);
     }
   }
+  if (op >= 6 && op <= 9 && P.n > 0) {
+    // the z stage becomes the real-to-real transform: last stage forward, first stage inverse
+    StageDesc& z = pipe == kPipeFwd ? P.st[P.n - 1] : P.st[0];
+    z.kind = op == 6 ? kDctZ : (op == 7 ? kIdctZ : (op == 8 ? kDstZ : kIdstZ));
+    z.tw2 = p->tw4_z;
+  }
   for (int s = 0; s < P.n; ++s) {
     StageDesc& d = P.st[s];
     if (d.kind == kPlain) d.prec = p->dtype;  // GBFFT_*_SPLIT values equal the StagePrec values
@@ -532,9 +539,11 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
   return P;
 }
 
+// ops 0-3: GBFFT_OP_*; 4, 5: Poisson (periodic, bounded z); 6-9: real-to-real
+// along z (DCT-II, DCT-III, DST-II, DST-III) with Fourier x and y
 static int pipe_of(int op) {
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT) return kPipeFwd;
-  if (op == GBFFT_OP_INVERSE || op == GBFFT_OP_ADJOINT) return kPipeInv;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 6 || op == 8) return kPipeFwd;
+  if (op == GBFFT_OP_INVERSE || op == GBFFT_OP_ADJOINT || op == 7 || op == 9) return kPipeInv;
   return kPipePoisson;
 }
 
@@ -1029,10 +1038,13 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   p->twn_y = upload_table(twiddle_table(ny, ny));
   p->twn_z = upload_table(twiddle_table(nz, nz));
   bool ok = p->tw_x && p->tw_y && p->tw_z && p->twn_x && p->twn_y && p->twn_z;
+  if (ok) {
+    p->tw4_z = upload_table(twiddle_table(4 * nz, nz + 1));
+    ok = p->tw4_z != nullptr;
+  }
   if (ok && kind == GBFFT_R2C) {
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
-    p->tw4_z = upload_table(twiddle_table(4 * nz, nz + 1));
-    ok = p->tw2 != nullptr && p->tw4_z != nullptr;
+    ok = p->tw2 != nullptr;
   }
   // persistent-launch counters: sized for the largest pipeline
   size_t words = 0;
@@ -1137,11 +1149,30 @@ int gbfft_exec_poisson_bounded(gbfft_plan plan, const void* in, void* out, void*
   return exec_poisson_op(plan, 5, in, out, stream);
 }
 
+int gbfft_exec_r2r_z(gbfft_plan plan, int r2r, int inverse, const void* in, void* out, void* stream) {
+  if (!plan || (r2r != GBFFT_R2R_DCT && r2r != GBFFT_R2R_DST) || (inverse != 0 && inverse != 1))
+    return GBFFT_ERR_INVALID_ARG;
+  const int op = 6 + 2 * r2r + inverse;
+  const int kind = op == 6 ? kDctZ : (op == 7 ? kIdctZ : (op == 8 ? kDstZ : kIdstZ));
+  if (!find_stage(plan->nz, inverse ? 1 : -1, kind)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  int rc = check_ptrs(in, out);
+  if (rc) return rc;
+  if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  rc = ensure_workspace(plan);
+  if (rc) return rc;
+  const int pipe = pipe_of(op);
+  Buf bin{const_cast<void*>(in), (long long)(op_in_bytes(plan, op) / sizeof(float2))};
+  Buf bout{out, (long long)(op_out_bytes(plan, op) / sizeof(float2))};
+  Pipeline P = build_pipeline(plan, pipe, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
+  return run_pipeline(plan, P, pipe, reinterpret_cast<cudaStream_t>(stream));
+}
+
 static size_t op_in_bytes(const gbfft_plan_s* p, int op) {
   const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);  // rowA complex per row
   const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
   if (p->kind == GBFFT_C2C) return spec_b;
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4 || op == 5) return real_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4 || op == 5 || op == 6 || op == 8)
+    return real_b;
   return spec_b;
 }
 
@@ -1149,7 +1180,7 @@ static size_t op_out_bytes(const gbfft_plan_s* p, int op) {
   const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);
   const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
   if (p->kind == GBFFT_C2C) return spec_b;
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT) return spec_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 6 || op == 8) return spec_b;
   return real_b;
 }
 

@@ -816,6 +816,26 @@ __device__ __forceinline__ void poisson_multiply(float2* sm, int gfirst, int ky_
 // position of element i of a pencil in the reordered sequence v
 __device__ __forceinline__ int dct_pos(int i, int L) { return (i & 1) ? L - 1 - (i >> 1) : (i >> 1); }
 
+// Pair (k, j = L - k) of the DCT-II post-processing: from V_k = A, V_j = B
+// (the FFT of the reordered pencil) to Y_k, Y_j.
+__device__ __forceinline__ void dct2_post_pair(float2 A, float2 B, float2 Wk, float2 Wj, float2& Yk, float2& Yj) {
+  auto one = [](float2 a, float2 b, float2 w) {
+    // Vr = (a + conj b) / 2, Vi = (a - conj b) / 2i; Y = 2 Re(w Vr) + 2 i Re(w Vi)
+    const float2 vr = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+    const float2 vi = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+    return make_float2(2.f * (w.x * vr.x - w.y * vr.y), 2.f * (w.x * vi.x - w.y * vi.y));
+  };
+  Yk = one(A, B, Wk);
+  Yj = one(B, A, Wj);
+}
+
+// Pair (k, j = L - k), k >= 1, of the DCT-III pre-processing:
+// V'_k = conj(W_k) (Yr_k - i Yr_j) + i conj(W_k) (Yi_k - i Yi_j) = conj(W_k) (Yr_k + Yi_j + i (Yi_k - Yr_j)).
+__device__ __forceinline__ void dct3_pre_pair(float2 Yk, float2 Yj, float2 Wk, float2 Wj, float2& Vk, float2& Vj) {
+  Vk = cmul(cconj(Wk), make_float2(Yk.x + Yj.y, Yk.y - Yj.x));
+  Vj = cmul(cconj(Wj), make_float2(Yj.x + Yk.y, Yj.y - Yk.x));
+}
+
 // DCT-II of every pencil's FFT (rows 0..L-1), multiply by the bounded Poisson
 // symbol, and prepare the DCT-III FFT input, pair (k, L - k) per item. The
 // symbol is -inv_n / (kx^2 + ky^2 + kz^2) with kz = k (cosine index), kx the
@@ -830,16 +850,8 @@ __device__ __forceinline__ void dct_poisson_bounded(float2* sm, const float2* w4
     const int j = k == 0 ? 0 : L - k;
     if (k > j) continue;  // the pair was taken by item (j, k)
     const float kx = (float)(gfirst + p);
-    const float2 A = sm[swz(k, p)], B = sm[swz(j, p)];
-    const float2 Wk = w4[k], Wj = w4[j];
-    auto forward = [](float2 a, float2 b, float2 w) {
-      // Vr = (a + conj b) / 2, Vi = (a - conj b) / 2i; Y = 2 Re(w Vr) + 2 i Re(w Vi)
-      const float2 vr = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-      const float2 vi = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
-      return make_float2(2.f * (w.x * vr.x - w.y * vr.y), 2.f * (w.x * vi.x - w.y * vi.y));
-    };
-    float2 Yk = forward(A, B, Wk);
-    float2 Yj = forward(B, A, Wj);
+    float2 Yk, Yj;
+    dct2_post_pair(sm[swz(k, p)], sm[swz(j, p)], w4[k], w4[j], Yk, Yj);
     const float kz_k = (float)k, kz_j = (float)j;
     const float k2k = kx * kx + ky * ky + kz_k * kz_k, k2j = kx * kx + ky * ky + kz_j * kz_j;
     Yk = cscale(Yk, k2k > 0.f ? -inv_n / k2k : 0.f);
@@ -847,12 +859,43 @@ __device__ __forceinline__ void dct_poisson_bounded(float2* sm, const float2* w4
     if (k == 0) {
       sm[swz(0, p)] = Yk;  // Y_L = 0 and W_0 = 1: V'_0 = Y_0
     } else {
-      // V'_k = conj(Wk) (Yr_k - i Yr_j) + i conj(Wk) (Yi_k - i Yi_j) = conj(Wk) (Yr_k + Yi_j + i (Yi_k - Yr_j))
-      const float2 uk = make_float2(Yk.x + Yj.y, Yk.y - Yj.x);
-      const float2 uj = make_float2(Yj.x + Yk.y, Yj.y - Yk.x);
-      sm[swz(k, p)] = cmul(cconj(Wk), uk);
-      if (j != k) sm[swz(j, p)] = cmul(cconj(Wj), uj);
+      float2 Vk, Vj;
+      dct3_pre_pair(Yk, Yj, w4[k], w4[j], Vk, Vj);
+      sm[swz(k, p)] = Vk;
+      if (j != k) sm[swz(j, p)] = Vj;
     }
+  }
+  __syncthreads();
+}
+
+// DCT-II post-processing alone (rows 0..L-1 become Y_0..Y_(L-1)), in place.
+template <int L, int THREADS>
+__device__ __forceinline__ void dct2_post(float2* sm, const float2* w4) {
+  constexpr int NPAIR = L / 2 + 1;
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    const int j = k == 0 ? 0 : L - k;
+    if (k > j) continue;
+    float2 Yk, Yj;
+    dct2_post_pair(sm[swz(k, p)], sm[swz(j, p)], w4[k], w4[j], Yk, Yj);
+    sm[swz(k, p)] = Yk;
+    if (j != k) sm[swz(j, p)] = Yj;
+  }
+  __syncthreads();
+}
+
+// DCT-III pre-processing alone (rows 0..L-1 hold Y, become the FFT input V'), in place.
+template <int L, int THREADS>
+__device__ __forceinline__ void dct3_pre(float2* sm, const float2* w4) {
+  constexpr int NPAIR = L / 2 + 1;
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    const int j = k == 0 ? 0 : L - k;
+    if (k > j || k == 0) continue;  // V'_0 = Y_0 stays
+    float2 Vk, Vj;
+    dct3_pre_pair(sm[swz(k, p)], sm[swz(j, p)], w4[k], w4[j], Vk, Vj);
+    sm[swz(k, p)] = Vk;
+    if (j != k) sm[swz(j, p)] = Vj;
   }
   __syncthreads();
 }
@@ -972,6 +1015,62 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
         n = it >> 4;
       }
       if (p < io.valid) st_data(io.gout + p * io.out_g + n * io.out_n, sm[swz(dct_pos(n, L), p)]);
+    }
+  } else if constexpr (KIND == kDctZ || KIND == kDstZ || KIND == kIdctZ || KIND == kIdstZ) {
+    // real-to-real along z (linear, so complex pencils transform their real and imaginary
+    // parts alike). DST-II(x)_k = DCT-II(s x)_(L-1-k) and DST-III(Y)_n = s_n DCT-III(reversed Y)_n,
+    // s_n = (-1)^n: the sine kinds flip signs and reverse order on the way in or out.
+    constexpr bool kFwd = KIND == kDctZ || KIND == kDstZ;
+    constexpr bool kSine = KIND == kDstZ || KIND == kIdstZ;
+    TileIO io_nos = io;
+    io_nos.scale = 1.f;
+    for (int it = threadIdx.x; it < L * 16; it += THREADS) {
+      int p, n;
+      if (row_in) {
+        n = it % L;
+        p = it / L;
+      } else {
+        p = it & 15;
+        n = it >> 4;
+      }
+      float2 a = (p < io.valid) ? ld_data(io.gin + p * io.in_g + n * io.in_n) : make_float2(0.f, 0.f);
+      int row;
+      if constexpr (kFwd) {
+        row = dct_pos(n, L);
+        if (kSine && (n & 1)) a = make_float2(-a.x, -a.y);
+      } else {
+        row = kSine ? L - 1 - n : n;
+      }
+      sm[swz(row, p)] = a;
+    }
+    __syncthreads();
+    if constexpr (kFwd) {
+      fft_passes<L, -1, THREADS, false, false, false>(sm, tw, io_nos);
+      dct2_post<L, THREADS>(sm, tw2);
+    } else {
+      dct3_pre<L, THREADS>(sm, tw2);
+      fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io_nos);
+    }
+    const float sc = io.scale;
+    for (int it = threadIdx.x; it < L * 16; it += THREADS) {
+      int p, n;
+      if (row_out) {
+        n = it % L;
+        p = it / L;
+      } else {
+        p = it & 15;
+        n = it >> 4;
+      }
+      if (p < io.valid) {
+        float2 v;
+        if constexpr (kFwd) {
+          v = sm[swz(kSine ? L - 1 - n : n, p)];
+        } else {
+          v = sm[swz(dct_pos(n, L), p)];
+          if (kSine && (n & 1)) v = make_float2(-v.x, -v.y);
+        }
+        st_data(io.gout + p * io.out_g + n * io.out_n, cscale(v, sc));
+      }
     }
   } else if constexpr (KIND == kPoissonZ) {
     // z pencils of the half spectrum: forward, multiply, inverse, in one tile

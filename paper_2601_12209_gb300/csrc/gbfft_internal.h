@@ -23,6 +23,10 @@ enum TileKind : int {
   kIdentity = 3,  // no arithmetic: pure pack/transpose/unpack (debug, bit-exact tests)
   kPoissonZ = 4,  // forward FFT, multiply by -1/|k|^2, inverse FFT (fused Poisson z stage)
   kPoissonZB = 5, // bounded z: DCT-II, multiply by -1/|k|^2, DCT-III (fused Poisson z stage, Neumann walls)
+  kDctZ = 6,      // real-to-real along z: DCT-II (REDFT10) of every pencil
+  kIdctZ = 7,     // DCT-III (REDFT01)
+  kDstZ = 8,      // DST-II (RODFT10)
+  kIdstZ = 9,     // DST-III (RODFT01)
 };
 
 // Arithmetic of a stage's radix-16 passes: FP32 on the CUDA cores, or dense

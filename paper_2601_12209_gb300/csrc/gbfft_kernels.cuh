@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(stage_threads(L, PREC), stage_min_blocks(L, PR
   float2* tw = sm + (L + 1) * kTileP;
   constexpr int TWL = tw_table_len(L);
   float2* tw2 = tw + TWL;
-  load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre || KIND == kPoissonZB);
+  load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre || KIND >= kPoissonZB);
   __syncthreads();
   if constexpr (stage_loops(L)) {
     for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {

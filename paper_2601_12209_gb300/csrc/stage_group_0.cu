@@ -8,8 +8,12 @@ namespace gbfft {
   v.push_back(make_stage_entry<L, -1, kPlain>());        \
   v.push_back(make_stage_entry<L, 1, kPlain>());         \
   v.push_back(make_stage_entry<L, -1, kIdentity>());     \
-  v.push_back(make_stage_entry<L, -1, kPoissonZ>());        \
-  v.push_back(make_stage_entry<L, -1, kPoissonZB>());
+  v.push_back(make_stage_entry<L, -1, kPoissonZ>());     \
+  v.push_back(make_stage_entry<L, -1, kPoissonZB>());    \
+  v.push_back(make_stage_entry<L, -1, kDctZ>());         \
+  v.push_back(make_stage_entry<L, 1, kIdctZ>());         \
+  v.push_back(make_stage_entry<L, -1, kDstZ>());         \
+  v.push_back(make_stage_entry<L, 1, kIdstZ>());
 #define GBFFT_STAGE_REAL(L)                              \
   v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
   v.push_back(make_stage_entry<L, 1, kC2RPre>());
