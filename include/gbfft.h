@@ -158,23 +158,32 @@ int gbfft_exec_poisson(gbfft_plan plan, const void* in, void* out, void* stream)
  */
 int gbfft_exec_poisson_bounded(gbfft_plan plan, const void* in, void* out, void* stream);
 
-/* real-to-real kinds along z (Section V-B: R2R transforms, DCT and DST) */
-#define GBFFT_R2R_DCT 0 /* forward DCT-II (FFTW REDFT10), inverse DCT-III (REDFT01) */
-#define GBFFT_R2R_DST 1 /* forward DST-II (RODFT10), inverse DST-III (RODFT01) */
+/* per-axis transform kinds (Section V-B: R2R transforms, DCT and DST) */
+#define GBFFT_R2R_NONE (-1) /* the axis keeps its Fourier transform */
+#define GBFFT_R2R_DCT 0     /* forward DCT-II (FFTW REDFT10), inverse DCT-III (REDFT01) */
+#define GBFFT_R2R_DST 1     /* forward DST-II (RODFT10), inverse DST-III (RODFT01) */
 
 /*
- * Real-to-real transform along z with Fourier transforms along x and y (the
- * spectral basis of the (Periodic, Periodic, Bounded) topology): forward
- * (inverse = 0) takes the plan's forward input (real [b][nz][ny][nx] for R2C
- * plans, complex for C2C) to a complex [b][nz][ny][nxc] array whose z index is
- * the cosine (DCT) or sine (DST) index k of
- *   DCT-II: Y_k = 2 sum_n x_n cos(pi k (2n + 1) / 2nz)
- *   DST-II: Y_k = 2 sum_n x_n sin(pi (k + 1) (2n + 1) / 2nz)
- * (unnormalised, x and y as gbfft_exec_forward); inverse = 1 applies DCT-III /
- * DST-III along z and the inverse x, y transforms, scaled by 1 / (2 nx ny nz),
- * so inverse(forward(x)) = x. Each z transform runs as one length-nz complex
- * FFT inside the z stage. Pencil or slab plans; the spectrum's layout is
+ * Mixed transform: along each axis (x, y, z) the DFT (GBFFT_R2R_NONE) or a
+ * real-to-real transform, each computed as one length-n complex FFT inside
+ * that axis's stage:
+ *   DCT-II: Y_k = 2 sum_n x_n cos(pi k (2n + 1) / 2n_ax)
+ *   DST-II: Y_k = 2 sum_n x_n sin(pi (k + 1) (2n + 1) / 2n_ax)
+ * Forward (inverse = 0) maps the plan's forward input to its spectrum shape,
+ * unscaled; inverse = 1 applies DCT-III / DST-III and inverse DFTs in reverse
+ * axis order, scaled by 1 / prod(2 n_ax for R2R axes, n_ax for DFT axes), so
+ * inverse(forward(x)) = x. Complex data transform their real and imaginary
+ * parts alike. R2C plans keep the DFT (R2C / C2R) along x: r2r_x must be
+ * GBFFT_R2R_NONE there. Pencil or slab plans; the spectrum's layout is
  * gbfft_exec_forward's (natural, or [b][kx][ky][kz] with GBFFT_TRANSPOSED_OUT).
+ */
+int gbfft_exec_r2r(gbfft_plan plan, int r2r_x, int r2r_y, int r2r_z, int inverse, const void* in, void* out,
+                   void* stream);
+
+/*
+ * gbfft_exec_r2r(plan, GBFFT_R2R_NONE, GBFFT_R2R_NONE, r2r, ...): Fourier x and y,
+ * DCT (r2r = GBFFT_R2R_DCT) or DST (GBFFT_R2R_DST) along z -- the spectral
+ * basis of the (Periodic, Periodic, Bounded) topology.
  */
 int gbfft_exec_r2r_z(gbfft_plan plan, int r2r, int inverse, const void* in, void* out, void* stream);
 

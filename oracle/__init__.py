@@ -310,28 +310,75 @@ def dst3_z(y) -> np.ndarray:
     return np.einsum("kn,...kyx->...nyx", _sin_matrix(n) * w[:, None], a)
 
 
-def r2r_z(x, kind: str = "dct", inverse: bool = False, nx: int | None = None, threads: int | None = None):
-    """Fourier along x (R2C for real input) and y, real-to-real along z (DCT-II / DST-II); inverse:
-    DCT-III / DST-III along z, inverse x and y transforms, scaled by 1 / (2 nx ny nz)."""
+def _along(a: np.ndarray, axis: int, fn) -> np.ndarray:
+    """Apply fn (acting on the last axis) along `axis`."""
+    return np.moveaxis(fn(np.moveaxis(a, axis, -1)), -1, axis)
+
+
+def _r2r_1d(a: np.ndarray, kind: str, inverse: bool) -> np.ndarray:
+    """DCT-II / DST-II (forward) or DCT-III / DST-III (inverse) along the last axis (matrix definitions)."""
+    n = a.shape[-1]
+    if kind == "dct":
+        M = _cos_matrix(n)
+        if inverse:
+            w = np.full(n, 2.0)
+            w[0] = 1.0
+            return np.einsum("...k,kn->...n", a, M * w[:, None])
+        return 2.0 * np.einsum("...n,kn->...k", a, M)
+    M = _sin_matrix(n)
+    if inverse:
+        w = np.full(n, 2.0)
+        w[-1] = 1.0
+        return np.einsum("...k,kn->...n", a, M * w[:, None])
+    return 2.0 * np.einsum("...n,kn->...k", a, M)
+
+
+def r2r(x, kinds=(None, None, "dct"), inverse: bool = False, nx: int | None = None,
+        threads: int | None = None) -> np.ndarray:
+    """Per-axis mixed transform of a grid [..., z, y, x]: kinds[axis] (axes x, y, z) is None (DFT),
+    "dct" (DCT-II forward, DCT-III inverse) or "dst" (DST-II / DST-III). Forward: unscaled, the x
+    axis of real input as R2C (bins 0..nx/2). Inverse: the transposed-order inverse of each axis,
+    C2R along x when `nx` is given, scaled by 1 / prod(2n for R2R axes, n for DFT axes)."""
+    kx, ky, kz = kinds
+    a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x)
     if not inverse:
-        a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x)
-        lead, (nz, ny, n_x) = a.shape[:-3], a.shape[-3:]
-        planes = a.reshape((-1, 1, ny, n_x))
-        if np.iscomplexobj(a):
-            S = fft3(planes.astype(np.complex128), threads=threads)
+        real = not np.iscomplexobj(a)
+        a = a.astype(np.float64 if real else np.complex128)
+        # x
+        if kx is None:
+            n = a.shape[-1]
+            a = fft1(a, threads=threads)
+            if real:
+                a = a[..., : n // 2 + 1]
         else:
-            S = rfft3(planes.astype(np.float64), threads=threads)
-        S = S.reshape(lead + (nz, ny, S.shape[-1]))
-        return dct2_z(S) if kind == "dct" else dst2_z(S)
-    a = np.asarray(x.detach().cpu().numpy() if hasattr(x, "detach") else x).astype(np.complex128)
-    lead, (nz, ny, nk) = a.shape[:-3], a.shape[-3:]
-    T = dct3_z(a) if kind == "dct" else dst3_z(a)
-    planes = T.reshape((-1, 1, ny, nk))
-    if nx is None:  # complex data: full x spectrum
-        out = fft3(planes, sign=+1, threads=threads).reshape(lead + (nz, ny, nk))
-        return out / (2.0 * nk * ny * nz)
-    out = c2r_unscaled(planes, nx, threads=threads).reshape(lead + (nz, ny, nx))
-    return out / (2.0 * nx * ny * nz)
+            a = _r2r_1d(a, kx, False)
+        for axis, k in ((-2, ky), (-3, kz)):
+            a = _along(a, axis, (lambda v: fft1(v, threads=threads)) if k is None else
+                       (lambda v, k=k: _r2r_1d(v, k, False)))
+        return a
+    a = a.astype(np.complex128)
+    scale = 1.0
+    for axis, k in ((-3, kz), (-2, ky)):
+        n = a.shape[axis]
+        scale *= n if k is None else 2 * n
+        a = _along(a, axis, (lambda v: fft1(v, sign=+1, threads=threads)) if k is None else
+                   (lambda v, k=k: _r2r_1d(v, k, True)))
+    if kx is None and nx is not None:
+        lead = a.shape[:-1]
+        a = c2r_unscaled(a.reshape((-1, 1, 1, a.shape[-1])), nx, threads=threads).reshape(lead + (nx,))
+        scale *= nx
+    elif kx is None:
+        scale *= a.shape[-1]
+        a = fft1(a, sign=+1, threads=threads)
+    else:
+        scale *= 2 * a.shape[-1]
+        a = _r2r_1d(a, kx, True)
+    return a / scale
+
+
+def r2r_z(x, kind: str = "dct", inverse: bool = False, nx: int | None = None, threads: int | None = None):
+    """Fourier along x (R2C for real input) and y, real-to-real along z: `r2r` with kinds (None, None, kind)."""
+    return r2r(x, (None, None, kind), inverse=inverse, nx=nx, threads=threads)
 
 
 def poisson_bounded_multiplier(nx: int, ny: int, nz: int) -> np.ndarray:

@@ -135,6 +135,13 @@ class Plan:
         Fourier x and y: forward takes the forward op's input to its spectrum shape; inverse undoes it."""
         if kind not in ("dct", "dst"):
             raise ValueError("kind must be 'dct' or 'dst'")
+        return self.r2r(x, (None, None, kind), inverse, out, stream)
+
+    def r2r(self, x, kinds=(None, None, "dct"), inverse: bool = False, out=None, stream=None):
+        """Per-axis transform (axes x, y, z): None = DFT, "dct" = DCT-II / DCT-III, "dst" = DST-II / DST-III."""
+        code = {None: abi.GBFFT_R2R_NONE, "dct": abi.GBFFT_R2R_DCT, "dst": abi.GBFFT_R2R_DST}
+        if len(kinds) != 3 or any(k not in code for k in kinds):
+            raise ValueError("kinds: three of None, 'dct', 'dst'")
         op = abi.GBFFT_OP_INVERSE if inverse else abi.GBFFT_OP_FORWARD
         idt, ishape, odt, oshape = self._io(op)
         _check_tensor(x, idt, ishape, "input")
@@ -144,8 +151,8 @@ class Plan:
                 out = out.view(oshape[1:])
         else:
             _check_tensor(out, odt, oshape, "out")
-        abi.gbfft_exec_r2r_z(self.handle, abi.GBFFT_R2R_DCT if kind == "dct" else abi.GBFFT_R2R_DST, inverse,
-                             x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        abi.gbfft_exec_r2r(self.handle, *(code[k] for k in kinds), inverse, x.data_ptr(), out.data_ptr(),
+                           _stream_handle(stream))
         return out
 
     def poisson(self, f, out=None, stream=None, bounded: bool = False):

@@ -31,6 +31,7 @@ GBFFT_OP_ADJOINT = 2
 GBFFT_OP_INVERSE_ADJOINT = 3
 GBFFT_OP_POISSON = 4  # gbfft_exec_host only
 GBFFT_OP_POISSON_BOUNDED = 5  # gbfft_exec_host only
+GBFFT_R2R_NONE = -1
 GBFFT_R2R_DCT = 0
 GBFFT_R2R_DST = 1
 GBFFT_OK = 0
@@ -49,7 +50,7 @@ GBFFT_NOALLOC_MAX_POINTS = 4194304
 EXPORTED = (
     "gbfft_plan_create", "gbfft_plan_get_cached", "gbfft_plan_cache_clear", "gbfft_exec",
     "gbfft_exec_forward", "gbfft_exec_inverse", "gbfft_exec_adjoint", "gbfft_exec_inverse_adjoint",
-    "gbfft_exec_poisson", "gbfft_exec_poisson_bounded", "gbfft_exec_r2r_z", "gbfft_exec_host", "gbfft_workspace_size", "gbfft_set_workspace",
+    "gbfft_exec_poisson", "gbfft_exec_poisson_bounded", "gbfft_exec_r2r_z", "gbfft_exec_r2r", "gbfft_exec_host", "gbfft_workspace_size", "gbfft_set_workspace",
     "gbfft_get_device_error", "gbfft_debug_run", "gbfft_strerror", "gbfft_plan_destroy",
     "gbfft_supported_length", "gbfft_radix_plan", "gbfft_version", "gbfft_exec_c2c_noalloc",
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
@@ -91,6 +92,7 @@ def load() -> ctypes.CDLL:
             "gbfft_exec_poisson": (i, [vp, vp, vp, vp]),
             "gbfft_exec_poisson_bounded": (i, [vp, vp, vp, vp]),
             "gbfft_exec_r2r_z": (i, [vp, i, i, vp, vp, vp]),
+            "gbfft_exec_r2r": (i, [vp, i, i, i, i, vp, vp, vp]),
             "gbfft_exec_host": (i, [vp, i, vp, vp]),
             "gbfft_workspace_size": (i, [vp, ctypes.POINTER(sz)]),
             "gbfft_set_workspace": (i, [vp, vp, sz]),
@@ -202,6 +204,11 @@ def gbfft_exec_inverse_adjoint(plan, in_ptr, out_ptr, stream=0):
 def gbfft_exec_poisson(plan, in_ptr, out_ptr, stream=0):
     _call("gbfft_exec_poisson", ctypes.c_void_p(plan), ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr),
           ctypes.c_void_p(stream))
+
+
+def gbfft_exec_r2r(plan, r2r_x, r2r_y, r2r_z, inverse, in_ptr, out_ptr, stream=0):
+    _call("gbfft_exec_r2r", ctypes.c_void_p(plan), int(r2r_x), int(r2r_y), int(r2r_z), int(bool(inverse)),
+          ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
 
 
 def gbfft_exec_r2r_z(plan, r2r, inverse, in_ptr, out_ptr, stream=0):

@@ -261,7 +261,7 @@ struct gbfft_plan_s {
   // twiddle tables (device)
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr, *tw2 = nullptr;
   float2 *twn_x = nullptr, *twn_y = nullptr, *twn_z = nullptr;  // natural W_L^m tables per axis
-  float2* tw4_z = nullptr;  // W_4nz^k, k <= nz: bounded-z (DCT) Poisson stage (R2C plans)
+  float2 *tw4_x = nullptr, *tw4_y = nullptr, *tw4_z = nullptr;  // W_4L^k, k <= L: DCT / DST stages per axis
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -373,7 +373,11 @@ static long long write_extent(const StageDesc& d) {
 // Layouts (float2 units; nxc = spectrum x bins):
 //   A natural input  [b][z][y][rowA]   B [b][z][kx][y]   C [b][kx][y][z]
 //   S natural spectrum [b][z][y][kx]
-static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin, Buf bout, Buf b1, Buf b2) {
+// r2r (optional): per axis x, y, z GBFFT_R2R_NONE (Fourier), GBFFT_R2R_DCT or
+// GBFFT_R2R_DST; those axes' stages become the real-to-real kinds (forward
+// op: type II, inverse op: type III, whose 2L factor joins the 1/N scale).
+static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin, Buf bout, Buf b1, Buf b2,
+                               const int* r2r = nullptr) {
   Pipeline P;
   const void* in = bin.p;
   void* out = bout.p;
@@ -437,7 +441,7 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
   } else if (pipe == kPipeInv) {
     const float interior = (op == GBFFT_OP_ADJOINT) ? 0.5f : 1.f;
     // the real-to-real inverses (DCT-III, DST-III) return 2 nz times the input along z
-    const float scale = (op == GBFFT_OP_INVERSE) ? invN : ((op == 7 || op == 9) ? 0.5f * invN : 1.f);
+    const float scale = (op == GBFFT_OP_INVERSE) ? invN : 1.f;
     if (!is_slab(p)) {
       void* Cb = r2c ? W1 : out;
       void* Bb = r2c ? W2 : W1;
@@ -525,11 +529,21 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
       add(Xi, 2, 1);
     }
   }
-  if (op >= 6 && op <= 9 && P.n > 0) {
-    // the z stage becomes the real-to-real transform: last stage forward, first stage inverse
-    StageDesc& z = pipe == kPipeFwd ? P.st[P.n - 1] : P.st[0];
-    z.kind = op == 6 ? kDctZ : (op == 7 ? kIdctZ : (op == 8 ? kDstZ : kIdstZ));
-    z.tw2 = p->tw4_z;
+  if (r2r && P.n == 3 && (pipe == kPipeFwd || pipe == kPipeInv)) {
+    // stages in axis order x, y, z forward and z, y, x inverse
+    const float2* tw4[3] = {p->tw4_x, p->tw4_y, p->tw4_z};
+    for (int ax = 0; ax < 3; ++ax) {
+      if (r2r[ax] != GBFFT_R2R_DCT && r2r[ax] != GBFFT_R2R_DST) continue;
+      StageDesc& d = P.st[pipe == kPipeFwd ? ax : 2 - ax];
+      const bool dct = r2r[ax] == GBFFT_R2R_DCT;
+      d.kind = pipe == kPipeFwd ? (dct ? kDct2 : kDst2) : (dct ? kDct3 : kDst3);
+      d.tw2 = tw4[ax];
+    }
+    if (pipe == kPipeInv) {
+      int n_r2r = 0;
+      for (int ax = 0; ax < 3; ++ax) n_r2r += (r2r[ax] == GBFFT_R2R_DCT || r2r[ax] == GBFFT_R2R_DST) ? 1 : 0;
+      P.st[2].scale *= 1.f / (float)(1 << n_r2r);  // DCT-III(DCT-II(x)) = 2L x
+    }
   }
   for (int s = 0; s < P.n; ++s) {
     StageDesc& d = P.st[s];
@@ -539,11 +553,10 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
   return P;
 }
 
-// ops 0-3: GBFFT_OP_*; 4, 5: Poisson (periodic, bounded z); 6-9: real-to-real
-// along z (DCT-II, DCT-III, DST-II, DST-III) with Fourier x and y
+// ops 0-3: GBFFT_OP_*; 4, 5: Poisson (periodic, bounded z)
 static int pipe_of(int op) {
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 6 || op == 8) return kPipeFwd;
-  if (op == GBFFT_OP_INVERSE || op == GBFFT_OP_ADJOINT || op == 7 || op == 9) return kPipeInv;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT) return kPipeFwd;
+  if (op == GBFFT_OP_INVERSE || op == GBFFT_OP_ADJOINT) return kPipeInv;
   return kPipePoisson;
 }
 
@@ -910,6 +923,8 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->twn_x);
   cudaFree(p->twn_y);
   cudaFree(p->twn_z);
+  cudaFree(p->tw4_x);
+  cudaFree(p->tw4_y);
   cudaFree(p->tw4_z);
   if (p->h_stream) cudaStreamDestroy(p->h_stream);
   for (auto& c : p->timed)
@@ -1039,8 +1054,10 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   p->twn_z = upload_table(twiddle_table(nz, nz));
   bool ok = p->tw_x && p->tw_y && p->tw_z && p->twn_x && p->twn_y && p->twn_z;
   if (ok) {
+    p->tw4_x = upload_table(twiddle_table(4 * Lx, Lx + 1));
+    p->tw4_y = upload_table(twiddle_table(4 * ny, ny + 1));
     p->tw4_z = upload_table(twiddle_table(4 * nz, nz + 1));
-    ok = p->tw4_z != nullptr;
+    ok = p->tw4_x && p->tw4_y && p->tw4_z;
   }
   if (ok && kind == GBFFT_R2C) {
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
@@ -1149,30 +1166,43 @@ int gbfft_exec_poisson_bounded(gbfft_plan plan, const void* in, void* out, void*
   return exec_poisson_op(plan, 5, in, out, stream);
 }
 
-int gbfft_exec_r2r_z(gbfft_plan plan, int r2r, int inverse, const void* in, void* out, void* stream) {
-  if (!plan || (r2r != GBFFT_R2R_DCT && r2r != GBFFT_R2R_DST) || (inverse != 0 && inverse != 1))
-    return GBFFT_ERR_INVALID_ARG;
-  const int op = 6 + 2 * r2r + inverse;
-  const int kind = op == 6 ? kDctZ : (op == 7 ? kIdctZ : (op == 8 ? kDstZ : kIdstZ));
-  if (!find_stage(plan->nz, inverse ? 1 : -1, kind)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+int gbfft_exec_r2r(gbfft_plan plan, int r2r_x, int r2r_y, int r2r_z, int inverse, const void* in, void* out,
+                   void* stream) {
+  if (!plan || (inverse != 0 && inverse != 1)) return GBFFT_ERR_INVALID_ARG;
+  const int r2r[3] = {r2r_x, r2r_y, r2r_z};
+  const int len[3] = {plan->nx, plan->ny, plan->nz};
+  for (int ax = 0; ax < 3; ++ax) {
+    if (r2r[ax] != GBFFT_R2R_NONE && r2r[ax] != GBFFT_R2R_DCT && r2r[ax] != GBFFT_R2R_DST)
+      return GBFFT_ERR_INVALID_ARG;
+    if (r2r[ax] == GBFFT_R2R_NONE) continue;
+    if (ax == 0 && plan->kind == GBFFT_R2C) return GBFFT_ERR_INVALID_ARG;  // x of an R2C plan is the real axis
+    const bool dct = r2r[ax] == GBFFT_R2R_DCT;
+    const int kind = inverse ? (dct ? kDct3 : kDst3) : (dct ? kDct2 : kDst2);
+    if (!find_stage(len[ax], inverse ? 1 : -1, kind)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  }
   int rc = check_ptrs(in, out);
   if (rc) return rc;
   if (cudaSetDevice(plan->device) != cudaSuccess) return GBFFT_ERR_CUDA;
   rc = ensure_workspace(plan);
   if (rc) return rc;
+  const int op = inverse ? GBFFT_OP_INVERSE : GBFFT_OP_FORWARD;
   const int pipe = pipe_of(op);
   Buf bin{const_cast<void*>(in), (long long)(op_in_bytes(plan, op) / sizeof(float2))};
   Buf bout{out, (long long)(op_out_bytes(plan, op) / sizeof(float2))};
-  Pipeline P = build_pipeline(plan, pipe, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1));
+  Pipeline P = build_pipeline(plan, pipe, op, bin, bout, ws_buf(plan, 0), ws_buf(plan, 1), r2r);
   return run_pipeline(plan, P, pipe, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gbfft_exec_r2r_z(gbfft_plan plan, int r2r, int inverse, const void* in, void* out, void* stream) {
+  if (r2r != GBFFT_R2R_DCT && r2r != GBFFT_R2R_DST) return GBFFT_ERR_INVALID_ARG;
+  return gbfft_exec_r2r(plan, GBFFT_R2R_NONE, GBFFT_R2R_NONE, r2r, inverse, in, out, stream);
 }
 
 static size_t op_in_bytes(const gbfft_plan_s* p, int op) {
   const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);  // rowA complex per row
   const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
   if (p->kind == GBFFT_C2C) return spec_b;
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4 || op == 5 || op == 6 || op == 8)
-    return real_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 4 || op == 5) return real_b;
   return spec_b;
 }
 
@@ -1180,7 +1210,7 @@ static size_t op_out_bytes(const gbfft_plan_s* p, int op) {
   const size_t real_b = (size_t)p->NA * p->batch * sizeof(float2);
   const size_t spec_b = (size_t)p->Nc * p->batch * sizeof(float2);
   if (p->kind == GBFFT_C2C) return spec_b;
-  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT || op == 6 || op == 8) return spec_b;
+  if (op == GBFFT_OP_FORWARD || op == GBFFT_OP_INVERSE_ADJOINT) return spec_b;
   return real_b;
 }
 

@@ -1016,12 +1016,12 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
       }
       if (p < io.valid) st_data(io.gout + p * io.out_g + n * io.out_n, sm[swz(dct_pos(n, L), p)]);
     }
-  } else if constexpr (KIND == kDctZ || KIND == kDstZ || KIND == kIdctZ || KIND == kIdstZ) {
-    // real-to-real along z (linear, so complex pencils transform their real and imaginary
+  } else if constexpr (KIND == kDct2 || KIND == kDst2 || KIND == kDct3 || KIND == kDst3) {
+    // real-to-real along the stage's axis (linear, so complex pencils transform their real and imaginary
     // parts alike). DST-II(x)_k = DCT-II(s x)_(L-1-k) and DST-III(Y)_n = s_n DCT-III(reversed Y)_n,
     // s_n = (-1)^n: the sine kinds flip signs and reverse order on the way in or out.
-    constexpr bool kFwd = KIND == kDctZ || KIND == kDstZ;
-    constexpr bool kSine = KIND == kDstZ || KIND == kIdstZ;
+    constexpr bool kFwd = KIND == kDct2 || KIND == kDst2;
+    constexpr bool kSine = KIND == kDst2 || KIND == kDst3;
     TileIO io_nos = io;
     io_nos.scale = 1.f;
     for (int it = threadIdx.x; it < L * 16; it += THREADS) {

@@ -23,10 +23,10 @@ enum TileKind : int {
   kIdentity = 3,  // no arithmetic: pure pack/transpose/unpack (debug, bit-exact tests)
   kPoissonZ = 4,  // forward FFT, multiply by -1/|k|^2, inverse FFT (fused Poisson z stage)
   kPoissonZB = 5, // bounded z: DCT-II, multiply by -1/|k|^2, DCT-III (fused Poisson z stage, Neumann walls)
-  kDctZ = 6,      // real-to-real along z: DCT-II (REDFT10) of every pencil
-  kIdctZ = 7,     // DCT-III (REDFT01)
-  kDstZ = 8,      // DST-II (RODFT10)
-  kIdstZ = 9,     // DST-III (RODFT01)
+  kDct2 = 6,      // real-to-real along the stage's axis: DCT-II (REDFT10) of every pencil
+  kDct3 = 7,      // DCT-III (REDFT01)
+  kDst2 = 8,      // DST-II (RODFT10)
+  kDst3 = 9,      // DST-III (RODFT01)
 };
 
 // Arithmetic of a stage's radix-16 passes: FP32 on the CUDA cores, or dense
@@ -73,7 +73,7 @@ struct StageDesc {
   float scale;     // multiplies every output value
   float interior;  // R2C/C2R: multiplies bins 1..L-1 of the half spectrum
   const float2* tw;    // packed per-pass twiddles of length L (tw_table_len(L) entries, device)
-  const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R); W_4L^k, k < L (bounded Poisson z)
+  const float2* tw2;   // W_2L^k = exp(-2 pi i k / 2L), k in [0, L] (R2C/C2R); W_4L^k, k <= L (DCT / DST kinds)
   int tw_len;          // entries of tw
   const float2* twn;   // natural twiddles W_L^m = exp(-2 pi i m / L), m in [0, L) (device)
   // Poisson z stage: wavenumber bookkeeping of the tile's pencils

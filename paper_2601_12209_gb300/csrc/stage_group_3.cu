@@ -10,10 +10,10 @@ namespace gbfft {
   v.push_back(make_stage_entry<L, -1, kIdentity>());     \
   v.push_back(make_stage_entry<L, -1, kPoissonZ>());     \
   v.push_back(make_stage_entry<L, -1, kPoissonZB>());    \
-  v.push_back(make_stage_entry<L, -1, kDctZ>());         \
-  v.push_back(make_stage_entry<L, 1, kIdctZ>());         \
-  v.push_back(make_stage_entry<L, -1, kDstZ>());         \
-  v.push_back(make_stage_entry<L, 1, kIdstZ>());
+  v.push_back(make_stage_entry<L, -1, kDct2>());         \
+  v.push_back(make_stage_entry<L, 1, kDct3>());         \
+  v.push_back(make_stage_entry<L, -1, kDst2>());         \
+  v.push_back(make_stage_entry<L, 1, kDst3>());
 #define GBFFT_STAGE_REAL(L)                              \
   v.push_back(make_stage_entry<L, -1, kR2CPost>());      \
   v.push_back(make_stage_entry<L, 1, kC2RPre>());
