@@ -104,7 +104,7 @@ __host__ __device__ constexpr int threads_for(int L) { return 16 * groups_for(L)
 // next to radix-16 ones) need more than 64 registers, so they take one block.
 __host__ __device__ constexpr int min_blocks_for(int L) {
   return L >= 1024 ? 1
-                   : (threads_for(L) >= 512 ? ((L & (L - 1)) ? 1 : 2) : (threads_for(L) >= 256 ? 3 : 4));
+                   : (threads_for(L) >= 512 ? ((L & (L - 1)) ? 1 : 2) : (threads_for(L) >= 256 ? (L == 256 ? 4 : 3) : 4));
 }
 
 // ---------------------------------------------------------- complex helpers
