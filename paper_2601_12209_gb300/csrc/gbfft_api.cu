@@ -590,6 +590,25 @@ static const PersistentKernel* find_persistent(const Pipeline& P) {
   return nullptr;
 }
 
+// Launch a stage kernel with programmatic stream serialization: it may start
+// while the previous kernel in the stream drains (the kernel waits for that
+// grid before it reads its input; see pdl_wait_prev).
+static cudaError_t launch_stage_kernel(const void* fn, long long grid, int threads, void** args, size_t smem,
+                                       cudaStream_t stream) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // Internal launch flag: run the stage with the warp-per-pencil kernel where one
 // is built (lengths 512 and 256 complex, the length-256 real x stages; FP32).
 constexpr unsigned kUseWarpKernel = 1u << 30;
@@ -619,8 +638,7 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags 
       const long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
       StageDesc dd = d;
       void* args[] = {&dd};
-      return cuda_err(cudaLaunchKernel(wk->fn, dim3((unsigned)grid), dim3((unsigned)wk->threads), args, wk->smem,
-                                       stream));
+      return cuda_err(launch_stage_kernel(wk->fn, grid, wk->threads, args, wk->smem, stream));
     }
   }
   if (!(flags & GBFFT_NO_TMA) && err && d.kind != kIdentity && d.prec == kPrecFP32) {
@@ -635,7 +653,7 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags 
       StageDesc dd = d;
       long long timeout_ns = 2000000000LL;
       void* args[] = {&map, &dd, &err, &timeout_ns};
-      e = cudaLaunchKernel(tk->fn, dim3((unsigned)grid), dim3((unsigned)tk->threads), args, tk->smem, stream);
+      e = launch_stage_kernel(tk->fn, grid, tk->threads, args, tk->smem, stream);
       return cuda_err(e);
     }
   }
@@ -648,7 +666,7 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags 
   long long grid = k->loops ? std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm) : d.n_tiles;
   StageDesc dd = d;
   void* args[] = {&dd};
-  e = cudaLaunchKernel(k->fn, dim3((unsigned)grid), dim3((unsigned)k->threads), args, k->smem, stream);
+  e = launch_stage_kernel(k->fn, grid, k->threads, args, k->smem, stream);
   return cuda_err(e);
 }
 

@@ -56,6 +56,15 @@ constexpr size_t stage_smem_bytes() {
 // it does not; the hardware block scheduler then hands out the tiles.
 __host__ __device__ constexpr bool stage_loops(int L) { return (L & (L - 1)) == 0; }
 
+// Programmatic dependent launch. Stage kernels are launched so that they may
+// start while the previous kernel in the stream drains: every block lets the
+// next grid launch (its blocks take SM slots as this grid's blocks retire, and
+// only once every block of this grid has started), runs its prologue (the
+// twiddle tables of the plan), then waits until the previous grid has
+// completed and its writes are visible before it reads its input.
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // The tensor-core passes hold a column group's accumulators across the
 // pass's barrier as well as the DFT-16 operand fragments: one block fewer.
 __host__ __device__ constexpr int stage_min_blocks(int L, int prec) {
@@ -77,8 +86,10 @@ __global__ void __launch_bounds__(stage_threads(L, PREC), stage_min_blocks(L, PR
   float2* tw = sm + (L + 1) * kTileP;
   constexpr int TWL = tw_table_len(L);
   float2* tw2 = tw + TWL;
+  pdl_launch_next();
   load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre || KIND >= kPoissonZB);
   __syncthreads();
+  pdl_wait_prev();
   if constexpr (stage_loops(L)) {
     for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
       process_tile<L, DIR, KIND, THREADS, PREC>(d, tile, sm, tw, tw2);

@@ -199,18 +199,22 @@ __global__ void __launch_bounds__(tma_threads(L), tma_blocks_per_sm(L))
   __shared__ __align__(8) uint64_t full[NB];
   __shared__ int s_fail;
   const long long stride = gridDim.x;
+  pdl_launch_next();
   if (threadIdx.x == 0) {
     tma_prefetch_map(&map);
     for (int i = 0; i < NB; ++i) mbar_init(&full[i], 1);
     mbar_init_fence();
     s_fail = 0;
+  }
+  load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre);
+  pdl_wait_prev();  // the first copies read the previous grid's output
+  if (threadIdx.x == 0) {
     for (int i = 0; i < NB; ++i) {
       const long long t = blockIdx.x + i * stride;
       if (t < d.n_tiles)
         tma_issue_tile<L, KIND, SRC>(&map, d, t, bufs + (size_t)i * (G::buf_bytes / 8), &full[i]);
     }
   }
-  load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre);
   __syncthreads();
   long long k = 0;
   for (long long t = blockIdx.x; t < d.n_tiles; t += stride, ++k) {

@@ -130,11 +130,13 @@ __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_ker
   float2* tws = sm + kTileP * RG;  // [k1][t] = W_L^(t k1), forward sign
   float2* w32 = tws + L;           // [c][k2'] = W_32^(c k2') = W_L^(R1 c k2')
   float2* tw2 = w32 + 32;          // W_2L^k, k <= L (real kinds)
+  pdl_launch_next();
   for (int i = threadIdx.x; i < L; i += kWarpThreads) tws[i] = d.twn[(i & 31) * (i >> 5)];
   if (threadIdx.x < 32) w32[threadIdx.x] = d.twn[(R1 * (threadIdx.x / R1) * (threadIdx.x % R1)) % L];
   if constexpr (kReal)
     for (int i = threadIdx.x; i <= L; i += kWarpThreads) tw2[i] = d.tw2[i];
   __syncthreads();
+  pdl_wait_prev();
   const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
   const int k1 = lane / C, c = lane % C;
   const int m = C == 2 ? c : ((c >> 1) + 2 * (c & 1));  // output block of this lane after step 5
