@@ -1558,9 +1558,13 @@ struct gbfft_many_s {
   std::vector<gbfft_plan> plans;  // one per grid: twiddles, and the separate-launch path
   std::vector<long long> offs;    // element offset of each grid in the packed buffers
   long long total = 0;            // complex elements of all grids
-  ManySegment* segs[2] = {nullptr, nullptr};  // forward, inverse
+  ManySegment* segs[2] = {nullptr, nullptr};  // forward, inverse; stage-major (one launch per stage)
   unsigned int* first[2] = {nullptr, nullptr};
   unsigned char* tile_seg[2] = {nullptr, nullptr};
+  // the one-launch queue's order: stage s of grid g at slot g + s (see gbfft_many_create)
+  ManySegment* segs_q[2] = {nullptr, nullptr};
+  unsigned int* first_q[2] = {nullptr, nullptr};
+  unsigned char* tile_seg_q[2] = {nullptr, nullptr};
   std::vector<unsigned int> first_host[2];
   unsigned int tiles[2] = {0, 0};
   int nseg = 0;
@@ -1578,6 +1582,9 @@ static void free_many(gbfft_many_s* m) {
     cudaFree(m->segs[i]);
     cudaFree(m->first[i]);
     cudaFree(m->tile_seg[i]);
+    cudaFree(m->segs_q[i]);
+    cudaFree(m->first_q[i]);
+    cudaFree(m->tile_seg_q[i]);
   }
   cudaFree(m->ws);
   cudaFree(m->ctl);
@@ -1689,7 +1696,41 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
   }
   m->nseg = 3 * count;
   m->counter_words = words;  // forward and inverse counters are laid out side by side
+  // Queue order of the one-launch schedule: stage s of grid g goes to slot g + s (z of grid t-2, y of grid
+  // t-1, x of grid t share slot t). Every dependency still has a smaller ticket, and the grids in flight
+  // at a time are about three, whose intermediates (tens of MB) stay in L2 between their stages, where
+  // the stage-major order of the per-stage launches streams every grid through HBM at every stage.
+  std::vector<ManySegment> segs_q[2];
+  std::vector<unsigned int> first_q[2];
+  for (int pipe = 0; pipe < 2; ++pipe) {
+    unsigned int acc = 0;
+    for (int slot = 0; slot < count + 2; ++slot)
+      for (int k = 2; k >= 0; --k) {
+        const int g = slot - k;
+        if (g < 0 || g >= count) continue;
+        const ManySegment& sg = segs[pipe][(size_t)k * count + g];
+        first_q[pipe].push_back(acc);
+        acc += (unsigned int)sg.d.n_tiles;
+        segs_q[pipe].push_back(sg);
+      }
+    first_q[pipe].push_back(acc);
+  }
   bool ok = true;
+  for (int pipe = 0; pipe < 2 && ok; ++pipe) {
+    ok = cudaMalloc(&m->segs_q[pipe], segs_q[pipe].size() * sizeof(ManySegment)) == cudaSuccess &&
+         cudaMemcpy(m->segs_q[pipe], segs_q[pipe].data(), segs_q[pipe].size() * sizeof(ManySegment),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMalloc(&m->first_q[pipe], first_q[pipe].size() * sizeof(unsigned int)) == cudaSuccess &&
+         cudaMemcpy(m->first_q[pipe], first_q[pipe].data(), first_q[pipe].size() * sizeof(unsigned int),
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+      std::vector<unsigned char> ts(m->tiles[pipe]);
+      for (size_t sg = 0; sg + 1 < first_q[pipe].size(); ++sg)
+        for (unsigned t = first_q[pipe][sg]; t < first_q[pipe][sg + 1]; ++t) ts[t] = (unsigned char)sg;
+      ok = cudaMalloc(&m->tile_seg_q[pipe], std::max<size_t>(ts.size(), 1)) == cudaSuccess &&
+           cudaMemcpy(m->tile_seg_q[pipe], ts.data(), ts.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
   for (int pipe = 0; pipe < 2 && ok; ++pipe) {
     ok = cudaMalloc(&m->segs[pipe], segs[pipe].size() * sizeof(ManySegment)) == cudaSuccess &&
          cudaMemcpy(m->segs[pipe], segs[pipe].data(), segs[pipe].size() * sizeof(ManySegment),
@@ -1739,9 +1780,9 @@ static int many_launch(gbfft_many m, int op, const void* in, void* out, void* st
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ManyArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.segs = m->segs[pipe];
-  a.first = m->first[pipe];
-  a.tile_seg = m->tile_seg[pipe];
+  a.segs = queue ? m->segs_q[pipe] : m->segs[pipe];
+  a.first = queue ? m->first_q[pipe] : m->first[pipe];
+  a.tile_seg = queue ? m->tile_seg_q[pipe] : m->tile_seg[pipe];
   a.nseg = m->nseg;
   a.total = m->tiles[pipe];
   a.in = reinterpret_cast<const float2*>(in);
