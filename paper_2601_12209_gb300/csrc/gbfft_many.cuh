@@ -3,11 +3,12 @@
 // The paper's runtime spawns every chunk task of every stage into one task
 // graph and lets ready tasks run wherever a worker is free (Sections III-C,
 // IV-C/D); the benefit it reports is largest when chunk costs are uneven
-// (Table II). Here the tasks of all grids share one ticket counter: tickets
-// run stage-major across grids (every grid's x tiles, then every grid's y
-// tiles, then z), so each dependency has a smaller ticket, and a grid's y
-// tiles start as soon as that grid's x planes are done, whatever the other
-// grids are doing.
+// (Table II). Here the tasks of all grids share one ticket counter. The
+// queue orders segments diagonally (stage s of grid g at slot g + s), so each
+// dependency has a smaller ticket, a grid's y tiles start as soon as that
+// grid's x planes are done, whatever the other grids are doing, and the few
+// grids in flight keep their intermediates in L2. The per-stage launches over
+// all grids (no waits) use the stage-major order of the same segments.
 //
 // Segments (one stage of one grid) live in device memory with buffer-relative
 // addresses, so a launch needs only the in / out / workspace base pointers and

@@ -57,7 +57,7 @@ def test_r2c_c2r_512(gb, mode):
 
 @pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
 def test_c2c_512(gb, mode):
-    """Spec target: C2C forward+inverse at 512^3, complex64 uniform[-1,1]."""
+    """C2C forward+inverse at 512^3, complex64 uniform[-1,1] (the headline C2C configuration)."""
     n = 512
     slab = mode == "slab"
     x = synth.uniform_complex((n, n, n), seed=3)
