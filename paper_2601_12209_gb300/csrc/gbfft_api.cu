@@ -261,6 +261,7 @@ struct gbfft_plan_s {
   // twiddle tables (device)
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr, *tw2 = nullptr;
   float2 *twn_x = nullptr, *twn_y = nullptr, *twn_z = nullptr;  // natural W_L^m tables per axis
+  float2* twn_real = nullptr;  // W_nx^m, m < nx: the real x stages' two-for-one transforms (R2C plans)
   float2 *tw4_x = nullptr, *tw4_y = nullptr, *tw4_z = nullptr;  // W_4L^k, k <= L: DCT / DST stages per axis
   // workspace
   void* ws = nullptr;
@@ -549,6 +550,7 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
     StageDesc& d = P.st[s];
     if (d.kind == kPlain) d.prec = p->dtype;  // GBFFT_*_SPLIT values equal the StagePrec values
     d.twn = d.tw == p->tw_x ? p->twn_x : (d.tw == p->tw_y ? p->twn_y : (d.tw == p->tw_z ? p->twn_z : nullptr));
+    if (d.kind == kR2CPost || d.kind == kC2RPre) d.twn = p->twn_real;  // length nx = 2 L
   }
   return P;
 }
@@ -941,6 +943,7 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->twn_x);
   cudaFree(p->twn_y);
   cudaFree(p->twn_z);
+  cudaFree(p->twn_real);
   cudaFree(p->tw4_x);
   cudaFree(p->tw4_y);
   cudaFree(p->tw4_z);
@@ -1079,7 +1082,8 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   }
   if (ok && kind == GBFFT_R2C) {
     p->tw2 = upload_table(twiddle_table(2 * Lx, Lx + 1));
-    ok = p->tw2 != nullptr;
+    p->twn_real = upload_table(twiddle_table(nx, nx));
+    ok = p->tw2 != nullptr && p->twn_real != nullptr;
   }
   // persistent-launch counters: sized for the largest pipeline
   size_t words = 0;

@@ -1,5 +1,6 @@
 // Warp-per-pencil stage kernels: complex lengths 512 and 256 (forward and
-// inverse) and the real-data x stages of length 256 (R2C split, C2R merge).
+// inverse), and the real x stages of 512-point rows (R2C, C2R) as two-for-one
+// length-512 complex transforms.
 #include "gbfft_warp.cuh"
 
 namespace gbfft {
@@ -9,8 +10,9 @@ void register_warp_group_0(std::vector<WarpKernel>& v) {
   v.push_back(make_warp_entry<512, 1, kPlain>());
   v.push_back(make_warp_entry<256, -1, kPlain>());
   v.push_back(make_warp_entry<256, 1, kPlain>());
-  v.push_back(make_warp_entry<256, -1, kR2CPost>());
-  v.push_back(make_warp_entry<256, 1, kC2RPre>());
+  // the real x stages of 512-point rows: two rows per length-512 complex FFT
+  v.push_back(make_pair_entry<512, -1>());
+  v.push_back(make_pair_entry<512, 1>());
 }
 
 }  // namespace gbfft
