@@ -110,9 +110,9 @@ __device__ __forceinline__ float2 mul_w4(float2 a) {
 
 // Column-side store of rows 0..NROWS-1 of the pencil-major tile: lanes run
 // along the 16 pencils of one element (one 128-byte line of global memory).
-template <int NROWS, int RG>
+template <int NROWS, int RG, int THREADS = kWarpThreads>
 __device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * kTileP; it += kWarpThreads) {
+  for (int it = threadIdx.x; it < NROWS * kTileP; it += THREADS) {
     const int q = it & 15, n = it >> 4;
     if (q < io.valid) st_data(io.gout + q + n * io.out_n, cscale(sm[q * RG + n], io.scale));
   }
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) pair_stage_kernel(StageDesc d
         __syncwarp();  // this warp's region is reused by the next tile
       } else {
         __syncthreads();
-        warp_col_store<RO, RO>(tile, io);
+        warp_col_store<RO, RO, kPairThreads>(tile, io);
         __syncthreads();
       }
     } else {
