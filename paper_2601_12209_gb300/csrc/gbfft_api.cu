@@ -171,7 +171,7 @@ static EncodeTiledFn encode_fn() {
 // Tensor map of a stage's input for the TMA kernel, or false when the layout
 // cannot be described (a stride or the base not a multiple of 16 bytes).
 //   row side:    dims {2 n_in floats, pencils, outer, batch}, box {32, 16, 1, 1}
-//   column side: dims {2 pencils floats, n_in, outer, batch}, box {32, 32, 1, 1}
+//   column side: dims {2 pencils floats, n_in, outer, batch}, box {32, kColBoxN, 1, 1}
 static bool encode_input_map(const StageDesc& d, int src, CUtensorMap* m) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
@@ -191,7 +191,7 @@ static bool encode_input_map(const StageDesc& d, int src, CUtensorMap* m) {
     dims[0] = 2ull * d.n_group;
     dims[1] = (cuuint64_t)d.n_in;
     strides_el[0] = d.in_n;
-    box[1] = 32;
+    box[1] = kColBoxN;
   }
   dims[2] = (cuuint64_t)d.n_outer;
   dims[3] = (cuuint64_t)d.batch;

@@ -19,7 +19,7 @@
 namespace gbfft {
 
 constexpr int kRowBoxN = 16;   // transform indices per row-side box
-constexpr int kColBoxN = 32;   // transform indices per column-side box
+constexpr int kColBoxN = 8;    // transform indices per column-side box (one 1 KB swizzle atom)
 constexpr int kRowBoxBytes = kRowBoxN * kTileP * 8;
 constexpr int kColBoxBytes = kColBoxN * kTileP * 8;
 
@@ -88,20 +88,21 @@ __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
 
 // Threads and resident blocks of the TMA kernel. Long pencils (512) get one
 // 1024-thread block per SM (one butterfly per thread per radix-8 pass) so 32
-// warps hide the arithmetic latency while the copies stream; shorter pencils
-// get two blocks per SM.
+// warps hide the arithmetic latency while the copies stream; length 256 gets
+// three blocks per SM (with 8-row column boxes its two-buffer ring fits), shorter
+// pencils two.
 __host__ __device__ constexpr int tma_threads(int L) {
   return L == 512 ? 1024 : (L >= 1024 ? 512 : threads_for(L));
 }
-__host__ __device__ constexpr int tma_blocks_per_sm(int L) { return L >= 512 ? 1 : 2; }
+__host__ __device__ constexpr int tma_blocks_per_sm(int L) { return L >= 512 ? 1 : (L == 256 ? 3 : 2); }
 
-template <int L, int KIND>
+template <int L, int KIND, int SRC>
 struct TmaGeom {
   static constexpr int n_in = KIND == kC2RPre ? L + 1 : L;
   static constexpr int rows_row = ((n_in + kRowBoxN - 1) / kRowBoxN) * kRowBoxN;
   static constexpr int rows_col = ((n_in + kColBoxN - 1) / kColBoxN) * kColBoxN;
   static constexpr int rows_min = (KIND == kR2CPost || KIND == kC2RPre) ? L + 1 : L;
-  static constexpr int rows_a = rows_row > rows_col ? rows_row : rows_col;
+  static constexpr int rows_a = SRC == kTmaRow ? rows_row : rows_col;
   static constexpr int rows_b = rows_a > rows_min ? rows_a : rows_min;
   static constexpr int rows = ((rows_b + 7) / 8) * 8;          // whole 1 KB swizzle atoms
   static constexpr int buf_bytes = rows * kTileP * 8;
@@ -120,7 +121,7 @@ struct TmaGeom {
 template <int L, int KIND, int SRC>
 __device__ __forceinline__ void tma_issue_tile(const CUtensorMap* map, const StageDesc& d, long long tile,
                                                float2* buf, uint64_t* bar) {
-  using G = TmaGeom<L, KIND>;
+  using G = TmaGeom<L, KIND, SRC>;
   // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
   const unsigned t32 = (unsigned)tile;
   const unsigned gc = t32 % (unsigned)d.n_gchunks;
@@ -186,7 +187,7 @@ __device__ __forceinline__ void process_tile_tma(const StageDesc& d, long long t
 template <int L, int DIR, int KIND, int SRC>
 __global__ void __launch_bounds__(tma_threads(L), tma_blocks_per_sm(L))
     tma_stage_kernel(const __grid_constant__ CUtensorMap map, StageDesc d, int* err, long long timeout_ns) {
-  using G = TmaGeom<L, KIND>;
+  using G = TmaGeom<L, KIND, SRC>;
   constexpr int THREADS = tma_threads(L);
   constexpr int NB = G::nbuf;
   extern __shared__ unsigned char smem_raw[];

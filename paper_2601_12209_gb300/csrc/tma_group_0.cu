@@ -7,7 +7,7 @@ namespace gbfft {
 template <int L, int DIR, int KIND, int SRC>
 static TmaKernel tma_entry() {
   return TmaKernel{L, DIR, KIND, SRC, reinterpret_cast<const void*>(&tma_stage_kernel<L, DIR, KIND, SRC>),
-                   tma_threads(L), TmaGeom<L, KIND>::smem};
+                   tma_threads(L), TmaGeom<L, KIND, SRC>::smem};
 }
 
 #define GBFFT_TMA_COMPLEX(L)                                  \
