@@ -29,6 +29,10 @@ struct PersistentKernel {
 };
 
 // A TMA stage kernel (gbfft_tma.cuh): input tiles arrive by tensor copies.
+// Tensor-copy boxes (shared by the kernels and the host's tensor maps)
+constexpr int kRowBoxN = 16;  // transform indices per row-side box
+constexpr int kColBoxN = 8;   // transform indices per column-side box (one 1 KB swizzle atom)
+
 struct TmaKernel {
   int L, dir, kind, src;  // src: 1 row-side copies, 2 column-side copies
   const void* fn;

@@ -18,8 +18,6 @@
 
 namespace gbfft {
 
-constexpr int kRowBoxN = 16;   // transform indices per row-side box
-constexpr int kColBoxN = 8;    // transform indices per column-side box (one 1 KB swizzle atom)
 constexpr int kRowBoxBytes = kRowBoxN * kTileP * 8;
 constexpr int kColBoxBytes = kColBoxN * kTileP * 8;
 
