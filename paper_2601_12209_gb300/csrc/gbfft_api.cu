@@ -627,6 +627,42 @@ static const WarpKernel* find_warp(const StageDesc& d) {
   return nullptr;
 }
 
+// Warp-per-pencil launches: when the column side of a stage is linear in
+// m = o * n_group + g (its outer stride is n_group group strides, as in the
+// natural spectrum [z][y][kx] read or written by the z stages), the outer and
+// group indices merge into one group axis of n_outer * n_group pencils. The
+// 16-pencil chunks then tile that axis with no ragged chunk per outer index
+// (nx/2 + 1 spectrum rows leave one of 17 chunks nearly empty otherwise), and
+// every chunk's 16 elements fill one aligned 128-byte line instead of
+// straddling two. A row side, if any, addresses its pencils through
+// (m / n_group, m % n_group).
+static void merge_pencils(StageDesc& d) {
+  if (d.n_outer <= 1) return;
+  const bool cin = d.in_mode == kCol, cout = d.out_mode == kCol;
+  if (!cin && !cout) return;
+  if (cin && d.in_o != (long long)d.n_group * d.in_g) return;
+  if (cout && d.out_o != (long long)d.n_group * d.out_g) return;
+  const long long m_total = (long long)d.n_outer * d.n_group;
+  if (m_total > 0x7FFFFFFFLL) return;
+  if (!cin) {
+    d.m_split = d.n_group;
+    d.split_o = d.in_o;
+    d.split_g = d.in_g;
+    d.in_g = 0;
+  } else if (!cout) {
+    d.m_split = d.n_group;
+    d.split_o = d.out_o;
+    d.split_g = d.out_g;
+    d.out_g = 0;
+  }
+  d.in_o = 0;
+  d.out_o = 0;
+  d.n_outer = 1;
+  d.n_group = (int)m_total;
+  d.n_gchunks = gchunks(d.n_group);
+  d.n_tiles = (long long)d.batch * d.n_gchunks;
+}
+
 // Launch one stage: the warp-per-pencil kernel when asked for and built, the
 // TMA kernel when one exists for the stage and its input layout can be
 // described by a tensor map, else the load/store kernel.
@@ -637,8 +673,9 @@ static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags 
       int bpsm = 1;
       cudaError_t e = launch_info(wk->fn, wk->threads, wk->smem, &bpsm);
       if (e != cudaSuccess) return GBFFT_ERR_CUDA;
-      const long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
       StageDesc dd = d;
+      if (d.kind == kPlain) merge_pencils(dd);
+      const long long grid = std::min<long long>(dd.n_tiles, (long long)sm_count() * bpsm);
       void* args[] = {&dd};
       return cuda_err(launch_stage_kernel(wk->fn, grid, wk->threads, args, wk->smem, stream));
     }

@@ -118,6 +118,15 @@ __device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& i
   }
 }
 
+// Offset of pencil p of the tile on a row side: p * stride_g, or, for a merged
+// descriptor (m_split > 0), the split of m = g0 + p into (m / m_split, m % m_split).
+__device__ __forceinline__ long long row_pencil(const StageDesc& d, int g0, int p, long long stride_g) {
+  if (d.m_split == 0) return (long long)p * stride_g;
+  const unsigned m = (unsigned)(g0 + p);
+  const unsigned o = m / (unsigned)d.m_split;
+  return (long long)o * d.split_o + (long long)(m - o * (unsigned)d.m_split) * d.split_g;
+}
+
 // Length 256 keeps 8 values per lane: three blocks per SM fit its registers.
 template <int L, int DIR, int KIND>
 __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_kernel(StageDesc d) {
@@ -152,7 +161,8 @@ __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_ker
         // the merge needs the pencil's L + 1 bins in its region first
         if (row_in) {
           for (int n = lane; n <= L; n += 32)
-            wr[n] = (p < io.valid) ? ld_data(io.gin + p * io.in_g + n * io.in_n) : make_float2(0.f, 0.f);
+            wr[n] = (p < io.valid) ? ld_data(io.gin + row_pencil(d, g0, p, io.in_g) + n * io.in_n)
+                                   : make_float2(0.f, 0.f);
           __syncwarp();
         } else {
           for (int it = threadIdx.x; it < (L + 1) * kTileP; it += kWarpThreads) {
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_ker
         __syncwarp();  // the transpose buffer overwrites the pencil
       } else {
         // lane t of warp p: x[t + 32 i] of pencil p (coalesced along the row)
-        const float2* src = io.gin + p * io.in_g;
+        const float2* src = io.gin + row_pencil(d, g0, p, io.in_g);
 #pragma unroll
         for (int i = 0; i < R1; ++i)
           v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_ker
       __syncwarp();
       if (row_out) {
         for (int n = lane; n <= L; n += 32)
-          if (p < io.valid) st_data(io.gout + p * io.out_g + n * io.out_n, cscale(wr[n], io.scale));
+          if (p < io.valid) st_data(io.gout + row_pencil(d, g0, p, io.out_g) + n * io.out_n, cscale(wr[n], io.scale));
         __syncwarp();
       } else {
         __syncthreads();
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_ker
       }
     } else if (row_out) {
       if (p < io.valid) {
-        float2* dst = io.gout + p * io.out_g;
+        float2* dst = io.gout + row_pencil(d, g0, p, io.out_g);
 #pragma unroll
         for (int k = 0; k < R1; ++k) st_data(dst + (k1 + R1 * k + R1 * R1 * m) * io.out_n, cscale(v[k], io.scale));
       }

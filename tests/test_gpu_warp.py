@@ -86,3 +86,26 @@ def test_warp_r2c_x_stage(gb, shape, slab):
     e_p = oracle.rel_l2(phi.cpu().numpy(), oracle.poisson(r.numpy()))
     print(f"[warp] r2c {shape} slab={slab}: fwd {e:.3e}, round trip {e_rt:.3e}, adjoint {e_adj:.3e}, poisson {e_p:.3e}")
     assert e < TOL and e_rt < TOL and e_adj < TOL and e_p < TOL
+
+
+@pytest.mark.parametrize("shape,slab,batch", [((20, 24, 512), False, 2), ((40, 6, 256), False, 1),
+                                              ((48, 20, 256), True, 2), ((30, 512, 512), False, 1)])
+def test_warp_merged_z_pencils(gb, shape, slab, batch):
+    """z stages whose spectrum side is the natural [z][y][kx] layout run with the outer (y)
+    and group (kx) indices merged into one pencil axis of ny * (nx/2+1) pencils: chunks that
+    cross a y row, a ragged last chunk, batch entries, and the in-place slab z stage."""
+    nx, ny, nz = shape
+    r = synth.normal_real((batch, nz, ny, nx), seed=80 + nx + nz)
+    p = gb.Plan(nx, ny, nz, kind="r2c", batch=batch, slab=slab)
+    _pin_warp(p)
+    s = p.forward(r.cuda())
+    back = p.inverse(s)
+    adj = p.adjoint(s)
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    e = oracle.rel_l2(s.cpu().numpy(), oracle.rfft3(r.numpy()))
+    e_rt = oracle.rel_l2(back.cpu().numpy(), r.numpy())
+    e_adj = oracle.rel_l2(adj.cpu().numpy(), oracle.r2c_adjoint(s.cpu().numpy().astype("complex128"), nx))
+    print(f"[warp] merged z {shape} slab={slab} batch={batch}: fwd {e:.3e}, round trip {e_rt:.3e}, "
+          f"adjoint {e_adj:.3e}")
+    assert e < TOL and e_rt < TOL and e_adj < TOL
