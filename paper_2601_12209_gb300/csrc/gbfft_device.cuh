@@ -754,6 +754,37 @@ __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float in
   __syncthreads();
 }
 
+// The R2C split fused with the column-side store of rows 0..M: the pair
+// (k, M-k) of pencil p is split from the transform in shared memory and both
+// bins go straight to global memory (lanes along the 16 pencils, one 128-byte
+// line per half-warp), with the same roundings as r2c_post then col_store but
+// without the shared-memory write-back and its barrier.
+template <int M, int THREADS>
+__device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float2* tw2, float interior,
+                                                   const TileIO& io) {
+  constexpr int NPAIR = M / 2 + 1;
+  const float sc = io.scale;
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    if (p >= io.valid) continue;
+    float2* g = io.gout + p;
+    if (k == 0) {
+      const float2 z0 = sm[swz(0, p)];
+      st_data(g, make_float2((z0.x + z0.y) * sc, 0.f * sc));
+      st_data(g + M * io.out_n, make_float2((z0.x - z0.y) * sc, 0.f * sc));
+    } else if (2 * k < M) {
+      const float2 A = sm[swz(k, p)], B = sm[swz(M - k, p)];
+      const float2 ze = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+      const float2 zo = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+      const float2 t = cmul(tw2[k], zo);
+      st_data(g + k * io.out_n, cscale(cscale(cadd(ze, t), interior), sc));
+      st_data(g + (M - k) * io.out_n, cscale(cscale(cconj(csub(ze, t)), interior), sc));
+    } else if (2 * k == M) {
+      st_data(g + k * io.out_n, cscale(cscale(cconj(sm[swz(k, p)]), interior), sc));
+    }
+  }
+}
+
 // C2R merge (in place, reads rows 0..M, writes rows 0..M-1): with
 // E = X[k] + conj X[M-k] and O = (X[k] - conj X[M-k]) exp(+i pi k/M),
 // Z[k] = E + i O; the inverse length-M FFT of Z gives x[2m] + i x[2m+1].
@@ -775,6 +806,37 @@ __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float int
       sm[swz(M - k, p)] = make_float2(e.x + o.y, -e.y + o.x);
     } else if (2 * k == M) {
       float2 xk = cscale(sm[swz(k, p)], interior);
+      sm[swz(k, p)] = make_float2(2.f * xk.x, -2.f * xk.y);
+    }
+  }
+  __syncthreads();
+}
+
+// The column-side load of bins 0..M fused with the C2R merge: the pair
+// (k, M-k) of pencil p is read from global memory (lanes along the pencils)
+// and merged into rows k and M-k of the tile, with the arithmetic of c2r_pre.
+// Ends with the barrier that orders the tile before the first pass.
+template <int M, int THREADS>
+__device__ __forceinline__ void col_load_c2r_pre(float2* sm, const float2* tw2, float interior, const TileIO& io) {
+  constexpr int NPAIR = M / 2 + 1;
+  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
+    const int p = it & 15, k = it >> 4;
+    const bool ok = p < io.valid;
+    const float2* g = io.gin + p;
+    if (k == 0) {
+      const float a = ok ? ld_data(g).x : 0.f, c = ok ? ld_data(g + M * io.in_n).x : 0.f;
+      sm[swz(0, p)] = make_float2(a + c, a - c);
+    } else if (2 * k < M) {
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 xk = cscale(ok ? ld_data(g + k * io.in_n) : z, interior);
+      const float2 xm = cscale(ok ? ld_data(g + (M - k) * io.in_n) : z, interior);
+      const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+      const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+      const float2 o = cmul(d, cconj(tw2[k]));
+      sm[swz(k, p)] = make_float2(e.x - o.y, e.y + o.x);
+      sm[swz(M - k, p)] = make_float2(e.x + o.y, -e.y + o.x);
+    } else if (2 * k == M) {
+      const float2 xk = cscale(ok ? ld_data(g + k * io.in_n) : make_float2(0.f, 0.f), interior);
       sm[swz(k, p)] = make_float2(2.f * xk.x, -2.f * xk.y);
     }
   }
@@ -974,15 +1036,21 @@ __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile,
     row_load<THREADS, L>(sm, io);
     __syncthreads();
     fft_passes<L, -1, THREADS, false, false, false>(sm, tw, io);
-    r2c_post<L, THREADS>(sm, tw2, d.interior);
-    if (row_out) row_store<THREADS, L + 1>(sm, io);
-    else col_store<THREADS, L + 1>(sm, io);
+    if (row_out) {
+      r2c_post<L, THREADS>(sm, tw2, d.interior);
+      row_store<THREADS, L + 1>(sm, io);
+    } else {
+      r2c_post_col_store<L, THREADS>(sm, tw2, d.interior, io);
+    }
   } else if constexpr (KIND == kC2RPre) {
     // L+1 half-spectrum bins -> L complex pairs of real output
-    if (row_in) row_load<THREADS, L + 1>(sm, io);
-    else col_load<THREADS, L + 1>(sm, io);
-    __syncthreads();
-    c2r_pre<L, THREADS>(sm, tw2, d.interior);
+    if (row_in) {
+      row_load<THREADS, L + 1>(sm, io);
+      __syncthreads();
+      c2r_pre<L, THREADS>(sm, tw2, d.interior);
+    } else {
+      col_load_c2r_pre<L, THREADS>(sm, tw2, d.interior, io);
+    }
     fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io);
     row_store<THREADS, L>(sm, io);
   } else if constexpr (KIND == kPoissonZB) {

@@ -156,9 +156,12 @@ __device__ __forceinline__ void process_tile_tma(const StageDesc& d, long long t
     }
   } else if constexpr (KIND == kR2CPost) {
     fft_passes<L, -1, THREADS, false, false, false, 0, SL>(sm, tw, io);
-    r2c_post<L, THREADS>(sm, tw2, d.interior);
-    if (row_out) row_store<THREADS, L + 1>(sm, io);
-    else col_store<THREADS, L + 1>(sm, io);
+    if (row_out) {
+      r2c_post<L, THREADS>(sm, tw2, d.interior);
+      row_store<THREADS, L + 1>(sm, io);
+    } else {
+      r2c_post_col_store<L, THREADS>(sm, tw2, d.interior, io);
+    }
   } else if constexpr (KIND == kC2RPre) {
     static_assert(SRC == kTmaCol, "the merge reads the column layout");
     c2r_pre<L, THREADS>(sm, tw2, d.interior);
