@@ -290,6 +290,8 @@ __device__ __forceinline__ int swz(int n, int p) { return (n << 4) + (p ^ ((n & 
 
 __device__ __forceinline__ float2 ld_data(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ void st_data(float2* p, float2 v) { __stcg(p, v); }
+__device__ __forceinline__ float4 ld_data4(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ void st_data4(float4* p, float4 v) { __stcg(p, v); }
 
 struct TileIO {
   const float2* gin;
@@ -724,46 +726,103 @@ __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const T
 
 // ---------------------------------------------------- real-transform phases
 
-// R2C split (in place in shared memory, rows 0..M): the length-M FFT Z of
-// z[m] = x[2m] + i x[2m+1] becomes X[k] = Ze[k] + W_2M^k Zo[k], k = 0..M, with
-// Ze = (Z[k] + conj Z[M-k])/2, Zo = (Z[k] - conj Z[M-k])/(2i). Pairs (k, M-k)
-// are handled by one thread. Bins 1..M-1 are scaled by `interior`.
+// R2C split of one pair (k, M-k), 0 < k < M/2: the length-M FFT Z of
+// z[m] = x[2m] + i x[2m+1] gives X[k] = Ze[k] + W_2M^k Zo[k] with
+// Ze = (Z[k] + conj Z[M-k])/2 and Zo = (Z[k] - conj Z[M-k])/(2i); X[M-k]
+// follows from the same Ze, Zo. A = Z[k], B = Z[M-k], w = W_2M^k.
+__device__ __forceinline__ void r2c_split_pair(float2 A, float2 B, float2 w, float2& xk, float2& xm) {
+  const float2 ze = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+  const float2 zo = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+  const float2 t = cmul(w, zo);
+  xk = cadd(ze, t);
+  xm = cconj(csub(ze, t));
+}
+
+// C2R merge of one pair (k, M-k), 0 < k < M/2: with E = X[k] + conj X[M-k]
+// and O = (X[k] - conj X[M-k]) conj(w), w = W_2M^k, Z[k] = E + i O and
+// Z[M-k] = conj(E) + i conj(O).
+__device__ __forceinline__ void c2r_merge_pair(float2 xk, float2 xm, float2 w, float2& zk, float2& zm) {
+  const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
+  const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
+  const float2 o = cmul(d, cconj(w));
+  zk = make_float2(e.x - o.y, e.y + o.x);
+  zm = make_float2(e.x + o.y, -e.y + o.x);
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// True when pencils p, p+1 (p even) of every row of the tile form one aligned
+// 16-byte chunk in global memory: a full tile, an even row stride and a
+// 16-byte aligned tile base.
+__device__ __forceinline__ bool pair_vec_ok(const float2* base, long long row_stride, int valid) {
+  return valid == kTileP && (row_stride & 1) == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0;
+}
+
+// R2C split (in place in shared memory, rows 0..M). Bins 1..M-1 are scaled by
+// `interior`. In the swizzled tile the pencils p, p+1 (p even) of a row share
+// one 16-byte chunk, so a thread takes the pair (k, M-k) of two pencils.
 template <int M, int THREADS>
 __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float interior) {
   constexpr int NPAIR = M / 2 + 1;
-  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
-    const int p = it & 15, k = it >> 4;
+  for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
+    const int p = (it & 7) << 1, k = it >> 3;
+    float4* rk = reinterpret_cast<float4*>(sm + swz(k, p));
     if (k == 0) {
-      float2 z0 = sm[swz(0, p)];
-      sm[swz(0, p)] = make_float2(z0.x + z0.y, 0.f);
-      sm[swz(M, p)] = make_float2(z0.x - z0.y, 0.f);
+      const float4 z0 = *rk;
+      *rk = make_float4(z0.x + z0.y, 0.f, z0.z + z0.w, 0.f);
+      *reinterpret_cast<float4*>(sm + swz(M, p)) = make_float4(z0.x - z0.y, 0.f, z0.z - z0.w, 0.f);
     } else if (2 * k < M) {
-      float2 A = sm[swz(k, p)], B = sm[swz(M - k, p)];
-      float2 ze = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-      float2 zo = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-      float2 t = cmul(tw2[k], zo);
-      float2 xk = cadd(ze, t);
-      float2 xm = cconj(csub(ze, t));
-      sm[swz(k, p)] = cscale(xk, interior);
-      sm[swz(M - k, p)] = cscale(xm, interior);
+      float4* rm = reinterpret_cast<float4*>(sm + swz(M - k, p));
+      const float4 A = *rk, B = *rm;
+      const float2 w = tw2[k];
+      float2 xk0, xm0, xk1, xm1;
+      r2c_split_pair(lo2(A), lo2(B), w, xk0, xm0);
+      r2c_split_pair(hi2(A), hi2(B), w, xk1, xm1);
+      *rk = cat2(cscale(xk0, interior), cscale(xk1, interior));
+      *rm = cat2(cscale(xm0, interior), cscale(xm1, interior));
     } else if (2 * k == M) {
-      float2 A = sm[swz(k, p)];
-      sm[swz(k, p)] = cscale(cconj(A), interior);
+      const float4 A = *rk;
+      *rk = cat2(cscale(cconj(lo2(A)), interior), cscale(cconj(hi2(A)), interior));
     }
   }
   __syncthreads();
 }
 
 // The R2C split fused with the column-side store of rows 0..M: the pair
-// (k, M-k) of pencil p is split from the transform in shared memory and both
-// bins go straight to global memory (lanes along the 16 pencils, one 128-byte
-// line per half-warp), with the same roundings as r2c_post then col_store but
-// without the shared-memory write-back and its barrier.
+// (k, M-k) is split from the transform in shared memory and both bins go
+// straight to global memory, with the roundings of r2c_post then col_store
+// but without the shared-memory write-back and its barrier. Full, aligned
+// tiles move two pencils per 16-byte access (8 lanes per 128-byte line).
 template <int M, int THREADS>
 __device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float2* tw2, float interior,
                                                    const TileIO& io) {
   constexpr int NPAIR = M / 2 + 1;
   const float sc = io.scale;
+  if (pair_vec_ok(io.gout, io.out_n, io.valid)) {
+    for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
+      const int p = (it & 7) << 1, k = it >> 3;
+      float4* g = reinterpret_cast<float4*>(io.gout + p);
+      const long long rk = (long long)k * (io.out_n >> 1), rm = (long long)(M - k) * (io.out_n >> 1);
+      const float4 A = *reinterpret_cast<const float4*>(sm + swz(k, p));
+      if (k == 0) {
+        st_data4(g, make_float4((A.x + A.y) * sc, 0.f * sc, (A.z + A.w) * sc, 0.f * sc));
+        st_data4(g + rm, make_float4((A.x - A.y) * sc, 0.f * sc, (A.z - A.w) * sc, 0.f * sc));
+      } else if (2 * k < M) {
+        const float4 B = *reinterpret_cast<const float4*>(sm + swz(M - k, p));
+        const float2 w = tw2[k];
+        float2 xk0, xm0, xk1, xm1;
+        r2c_split_pair(lo2(A), lo2(B), w, xk0, xm0);
+        r2c_split_pair(hi2(A), hi2(B), w, xk1, xm1);
+        st_data4(g + rk, cat2(cscale(cscale(xk0, interior), sc), cscale(cscale(xk1, interior), sc)));
+        st_data4(g + rm, cat2(cscale(cscale(xm0, interior), sc), cscale(cscale(xm1, interior), sc)));
+      } else if (2 * k == M) {
+        st_data4(g + rk, cat2(cscale(cscale(cconj(lo2(A)), interior), sc), cscale(cscale(cconj(hi2(A)), interior), sc)));
+      }
+    }
+    return;
+  }
   for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
     const int p = it & 15, k = it >> 4;
     if (p >= io.valid) continue;
@@ -773,70 +832,93 @@ __device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float
       st_data(g, make_float2((z0.x + z0.y) * sc, 0.f * sc));
       st_data(g + M * io.out_n, make_float2((z0.x - z0.y) * sc, 0.f * sc));
     } else if (2 * k < M) {
-      const float2 A = sm[swz(k, p)], B = sm[swz(M - k, p)];
-      const float2 ze = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-      const float2 zo = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-      const float2 t = cmul(tw2[k], zo);
-      st_data(g + k * io.out_n, cscale(cscale(cadd(ze, t), interior), sc));
-      st_data(g + (M - k) * io.out_n, cscale(cscale(cconj(csub(ze, t)), interior), sc));
+      float2 xk, xm;
+      r2c_split_pair(sm[swz(k, p)], sm[swz(M - k, p)], tw2[k], xk, xm);
+      st_data(g + k * io.out_n, cscale(cscale(xk, interior), sc));
+      st_data(g + (M - k) * io.out_n, cscale(cscale(xm, interior), sc));
     } else if (2 * k == M) {
       st_data(g + k * io.out_n, cscale(cscale(cconj(sm[swz(k, p)]), interior), sc));
     }
   }
 }
 
-// C2R merge (in place, reads rows 0..M, writes rows 0..M-1): with
-// E = X[k] + conj X[M-k] and O = (X[k] - conj X[M-k]) exp(+i pi k/M),
-// Z[k] = E + i O; the inverse length-M FFT of Z gives x[2m] + i x[2m+1].
-// Only the real parts of X[0] and X[M] enter (the Hermitian projection).
+// C2R merge (in place, reads rows 0..M, writes rows 0..M-1). Only the real
+// parts of X[0] and X[M] enter (the Hermitian projection); the inverse
+// length-M FFT of Z then gives x[2m] + i x[2m+1]. Pencil pairs as in r2c_post.
 template <int M, int THREADS>
 __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float interior) {
   constexpr int NPAIR = M / 2 + 1;
-  for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
-    const int p = it & 15, k = it >> 4;
+  for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
+    const int p = (it & 7) << 1, k = it >> 3;
+    float4* rk = reinterpret_cast<float4*>(sm + swz(k, p));
     if (k == 0) {
-      float a = sm[swz(0, p)].x, c = sm[swz(M, p)].x;
-      sm[swz(0, p)] = make_float2(a + c, a - c);
+      const float4 a = *rk, c = *reinterpret_cast<const float4*>(sm + swz(M, p));
+      *rk = make_float4(a.x + c.x, a.x - c.x, a.z + c.z, a.z - c.z);
     } else if (2 * k < M) {
-      float2 xk = cscale(sm[swz(k, p)], interior), xm = cscale(sm[swz(M - k, p)], interior);
-      float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
-      float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
-      float2 o = cmul(d, cconj(tw2[k]));
-      sm[swz(k, p)] = make_float2(e.x - o.y, e.y + o.x);
-      sm[swz(M - k, p)] = make_float2(e.x + o.y, -e.y + o.x);
+      float4* rm = reinterpret_cast<float4*>(sm + swz(M - k, p));
+      const float4 A = *rk, B = *rm;
+      const float2 w = tw2[k];
+      float2 zk0, zm0, zk1, zm1;
+      c2r_merge_pair(cscale(lo2(A), interior), cscale(lo2(B), interior), w, zk0, zm0);
+      c2r_merge_pair(cscale(hi2(A), interior), cscale(hi2(B), interior), w, zk1, zm1);
+      *rk = cat2(zk0, zk1);
+      *rm = cat2(zm0, zm1);
     } else if (2 * k == M) {
-      float2 xk = cscale(sm[swz(k, p)], interior);
-      sm[swz(k, p)] = make_float2(2.f * xk.x, -2.f * xk.y);
+      const float2 x0 = cscale(lo2(*rk), interior), x1 = cscale(hi2(*rk), interior);
+      *rk = make_float4(2.f * x0.x, -2.f * x0.y, 2.f * x1.x, -2.f * x1.y);
     }
   }
   __syncthreads();
 }
 
 // The column-side load of bins 0..M fused with the C2R merge: the pair
-// (k, M-k) of pencil p is read from global memory (lanes along the pencils)
-// and merged into rows k and M-k of the tile, with the arithmetic of c2r_pre.
-// Ends with the barrier that orders the tile before the first pass.
+// (k, M-k) is read from global memory and merged into rows k and M-k of the
+// tile, with the arithmetic of c2r_pre. Full, aligned tiles read two pencils
+// per 16-byte access. Ends with the barrier that orders the tile before the
+// first pass.
 template <int M, int THREADS>
 __device__ __forceinline__ void col_load_c2r_pre(float2* sm, const float2* tw2, float interior, const TileIO& io) {
   constexpr int NPAIR = M / 2 + 1;
+  if (pair_vec_ok(io.gin, io.in_n, io.valid)) {
+    for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
+      const int p = (it & 7) << 1, k = it >> 3;
+      const float4* g = reinterpret_cast<const float4*>(io.gin + p);
+      const long long rk = (long long)k * (io.in_n >> 1), rm = (long long)(M - k) * (io.in_n >> 1);
+      float4* sk = reinterpret_cast<float4*>(sm + swz(k, p));
+      if (k == 0) {
+        const float4 a = ld_data4(g), c = ld_data4(g + rm);
+        *sk = make_float4(a.x + c.x, a.x - c.x, a.z + c.z, a.z - c.z);
+      } else if (2 * k < M) {
+        const float4 A = ld_data4(g + rk), B = ld_data4(g + rm);
+        const float2 w = tw2[k];
+        float2 zk0, zm0, zk1, zm1;
+        c2r_merge_pair(cscale(lo2(A), interior), cscale(lo2(B), interior), w, zk0, zm0);
+        c2r_merge_pair(cscale(hi2(A), interior), cscale(hi2(B), interior), w, zk1, zm1);
+        *sk = cat2(zk0, zk1);
+        *reinterpret_cast<float4*>(sm + swz(M - k, p)) = cat2(zm0, zm1);
+      } else if (2 * k == M) {
+        const float4 A = ld_data4(g + rk);
+        const float2 x0 = cscale(lo2(A), interior), x1 = cscale(hi2(A), interior);
+        *sk = make_float4(2.f * x0.x, -2.f * x0.y, 2.f * x1.x, -2.f * x1.y);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int it = threadIdx.x; it < NPAIR * 16; it += THREADS) {
     const int p = it & 15, k = it >> 4;
     const bool ok = p < io.valid;
     const float2* g = io.gin + p;
+    const float2 z = make_float2(0.f, 0.f);
     if (k == 0) {
       const float a = ok ? ld_data(g).x : 0.f, c = ok ? ld_data(g + M * io.in_n).x : 0.f;
       sm[swz(0, p)] = make_float2(a + c, a - c);
     } else if (2 * k < M) {
-      const float2 z = make_float2(0.f, 0.f);
       const float2 xk = cscale(ok ? ld_data(g + k * io.in_n) : z, interior);
       const float2 xm = cscale(ok ? ld_data(g + (M - k) * io.in_n) : z, interior);
-      const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);
-      const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);
-      const float2 o = cmul(d, cconj(tw2[k]));
-      sm[swz(k, p)] = make_float2(e.x - o.y, e.y + o.x);
-      sm[swz(M - k, p)] = make_float2(e.x + o.y, -e.y + o.x);
+      c2r_merge_pair(xk, xm, tw2[k], sm[swz(k, p)], sm[swz(M - k, p)]);
     } else if (2 * k == M) {
-      const float2 xk = cscale(ok ? ld_data(g + k * io.in_n) : make_float2(0.f, 0.f), interior);
+      const float2 xk = cscale(ok ? ld_data(g + k * io.in_n) : z, interior);
       sm[swz(k, p)] = make_float2(2.f * xk.x, -2.f * xk.y);
     }
   }

@@ -94,8 +94,10 @@ def test_config1_tiny_c2c_64(gb):
     assert err("cfg1 fwd full", Xh, oracle.fft3(xn)) < TOL
 
 
+# odd ny (odd column strides, odd spectrum size per batch entry) and a ragged last tile after
+# full ones: the real x stages switch between their two-pencil and one-pencil access paths
 R2C_SHAPES = [(8, 8, 8, 1), (64, 64, 64, 1), (16, 12, 10, 2), (60, 48, 80, 1), (32, 20, 24, 1), (128, 30, 16, 1),
-              (256, 16, 8, 1)]
+              (256, 16, 8, 1), (32, 15, 5, 2), (16, 40, 3, 2)]
 
 
 @pytest.mark.parametrize("shape", R2C_SHAPES, ids=lambda s: "x".join(map(str, s)))
