@@ -880,28 +880,46 @@ template <int M, int THREADS>
 __device__ __forceinline__ void col_load_c2r_pre(float2* sm, const float2* tw2, float interior, const TileIO& io) {
   constexpr int NPAIR = M / 2 + 1;
   if (pair_vec_ok(io.gin, io.in_n, io.valid)) {
-    for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
-      const int p = (it & 7) << 1, k = it >> 3;
-      const float4* g = reinterpret_cast<const float4*>(io.gin + p);
-      const long long rk = (long long)k * (io.in_n >> 1), rm = (long long)(M - k) * (io.in_n >> 1);
-      float4* sk = reinterpret_cast<float4*>(sm + swz(k, p));
-      if (k == 0) {
-        const float4 a = ld_data4(g), c = ld_data4(g + rm);
-        *sk = make_float4(a.x + c.x, a.x - c.x, a.z + c.z, a.z - c.z);
-      } else if (2 * k < M) {
-        const float4 A = ld_data4(g + rk), B = ld_data4(g + rm);
-        const float2 w = tw2[k];
-        float2 zk0, zm0, zk1, zm1;
-        c2r_merge_pair(cscale(lo2(A), interior), cscale(lo2(B), interior), w, zk0, zm0);
-        c2r_merge_pair(cscale(hi2(A), interior), cscale(hi2(B), interior), w, zk1, zm1);
-        *sk = cat2(zk0, zk1);
-        *reinterpret_cast<float4*>(sm + swz(M - k, p)) = cat2(zm0, zm1);
-      } else if (2 * k == M) {
-        const float4 A = ld_data4(g + rk);
-        const float2 x0 = cscale(lo2(A), interior), x1 = cscale(hi2(A), interior);
-        *sk = make_float4(2.f * x0.x, -2.f * x0.y, 2.f * x1.x, -2.f * x1.y);
-      }
-    }
+    // the loads of CH consecutive pairs of the thread are issued before their
+    // merges, so the thread waits for one global-memory latency per CH pairs
+    constexpr int ITERS = (NPAIR * 8 + THREADS - 1) / THREADS;
+    constexpr int CH = 1;
+    static_for<(ITERS + CH - 1) / CH>([&](auto cc) {
+      constexpr int c0 = decltype(cc)::value * CH;
+      float4 A[CH], B[CH];
+      static_for<CH>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const int it = threadIdx.x + (c0 + i) * THREADS;
+        if (c0 + i < ITERS && it < NPAIR * 8) {
+          const int p = (it & 7) << 1, k = it >> 3;
+          const float4* g = reinterpret_cast<const float4*>(io.gin + p);
+          A[i] = ld_data4(g + (long long)k * (io.in_n >> 1));
+          B[i] = ld_data4(g + (long long)(M - k) * (io.in_n >> 1));  // k = 0: row M; 2k = M: row k again
+        }
+      });
+      static_for<CH>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const int it = threadIdx.x + (c0 + i) * THREADS;
+        if (c0 + i < ITERS && it < NPAIR * 8) {
+          const int p = (it & 7) << 1, k = it >> 3;
+          float4* sk = reinterpret_cast<float4*>(sm + swz(k, p));
+          const float4 a = A[i], c = B[i];
+          if (k == 0) {
+            *sk = make_float4(a.x + c.x, a.x - c.x, a.z + c.z, a.z - c.z);
+          } else if (2 * k < M) {
+            const float2 w = tw2[k];
+            float2 zk0, zm0, zk1, zm1;
+            c2r_merge_pair(cscale(lo2(a), interior), cscale(lo2(c), interior), w, zk0, zm0);
+            c2r_merge_pair(cscale(hi2(a), interior), cscale(hi2(c), interior), w, zk1, zm1);
+            *sk = cat2(zk0, zk1);
+            *reinterpret_cast<float4*>(sm + swz(M - k, p)) = cat2(zm0, zm1);
+          } else if (2 * k == M) {
+            const float2 x0 = cscale(lo2(a), interior), x1 = cscale(hi2(a), interior);
+            *sk = make_float4(2.f * x0.x, -2.f * x0.y, 2.f * x1.x, -2.f * x1.y);
+          }
+        }
+      });
+    });
     __syncthreads();
     return;
   }
