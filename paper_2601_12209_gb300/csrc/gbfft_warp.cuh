@@ -110,11 +110,12 @@ __device__ __forceinline__ float2 mul_w4(float2 a) {
 
 // Column-side store of rows 0..NROWS-1 of the pencil-major tile: lanes run
 // along the 16 pencils of one element (one 128-byte line of global memory).
-template <int NROWS, int RG, int THREADS = kWarpThreads>
+// Element n of a pencil sits at n + (n >> PAD_SHIFT) * PAD of its region.
+template <int NROWS, int RG, int THREADS = kWarpThreads, int PAD_SHIFT = 0, int PAD = 0>
 __device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& io) {
   for (int it = threadIdx.x; it < NROWS * kTileP; it += THREADS) {
     const int q = it & 15, n = it >> 4;
-    if (q < io.valid) st_data(io.gout + q + n * io.out_n, cscale(sm[q * RG + n], io.scale));
+    if (q < io.valid) st_data(io.gout + q + n * io.out_n, cscale(sm[q * RG + n + (n >> PAD_SHIFT) * PAD], io.scale));
   }
 }
 
@@ -251,10 +252,15 @@ __global__ void __launch_bounds__(kWarpThreads, L == 256 ? 3 : 2) warp_stage_ker
       else __syncwarp();             // this warp's region is reused by the next tile
     } else {
       __syncwarp();  // every lane has read the transpose buffer
+      // the lanes of one half-warp differ in k1 and m; each block of R1^2
+      // elements is shifted by 16 / C slots so that they hit distinct banks
+      constexpr int kPadShift = R1 == 16 ? 8 : 6, kPad = 16 / C;
+      static_assert(R1 * R1 == (1 << kPadShift), "R1^2 elements per output block");
+      static_assert(L + (C - 1) * kPad <= RG, "padded pencil fits its region");
 #pragma unroll
-      for (int k = 0; k < R1; ++k) wr[k1 + R1 * k + R1 * R1 * m] = v[k];
+      for (int k = 0; k < R1; ++k) wr[k1 + R1 * k + R1 * R1 * m + m * kPad] = v[k];
       __syncthreads();
-      warp_col_store<L, RG>(sm, io);
+      warp_col_store<L, RG, kWarpThreads, kPadShift, kPad>(sm, io);
       __syncthreads();
     }
   }
