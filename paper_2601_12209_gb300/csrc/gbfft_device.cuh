@@ -871,6 +871,77 @@ __device__ __forceinline__ void c2r_pre(float2* sm, const float2* tw2, float int
   __syncthreads();
 }
 
+// The fused C2R column load for full, aligned tiles (pair_vec_ok), split so
+// that a tile loop can issue part of a tile's loads early: the first kEarly
+// of the thread's pairs (k, M-k) of two pencils are read into A, B ahead of
+// time, the rest when the tile is merged into rows k and M-k.
+template <int M, int THREADS>
+struct C2REarlyLoads {
+  static constexpr int kIters = ((M / 2 + 1) * 8 + THREADS - 1) / THREADS;
+  static constexpr int kEarly = 1;
+  float4 A[kEarly], B[kEarly];
+};
+
+template <int M>
+__device__ __forceinline__ void c2r_load_pair(const TileIO& io, int it, float4& a, float4& b) {
+  const int p = (it & 7) << 1, k = it >> 3;
+  const float4* g = reinterpret_cast<const float4*>(io.gin + p);
+  a = ld_data4(g + (long long)k * (io.in_n >> 1));
+  b = ld_data4(g + (long long)(M - k) * (io.in_n >> 1));  // k = 0: row M; 2k = M: row k again
+}
+
+template <int M>
+__device__ __forceinline__ void c2r_merge_pair_to(float2* sm, const float2* tw2, float interior, int it, float4 a,
+                                                  float4 c) {
+  const int p = (it & 7) << 1, k = it >> 3;
+  float4* sk = reinterpret_cast<float4*>(sm + swz(k, p));
+  if (k == 0) {
+    *sk = make_float4(a.x + c.x, a.x - c.x, a.z + c.z, a.z - c.z);
+  } else if (2 * k < M) {
+    const float2 w = tw2[k];
+    float2 zk0, zm0, zk1, zm1;
+    c2r_merge_pair(cscale(lo2(a), interior), cscale(lo2(c), interior), w, zk0, zm0);
+    c2r_merge_pair(cscale(hi2(a), interior), cscale(hi2(c), interior), w, zk1, zm1);
+    *sk = cat2(zk0, zk1);
+    *reinterpret_cast<float4*>(sm + swz(M - k, p)) = cat2(zm0, zm1);
+  } else if (2 * k == M) {
+    const float2 x0 = cscale(lo2(a), interior), x1 = cscale(hi2(a), interior);
+    *sk = make_float4(2.f * x0.x, -2.f * x0.y, 2.f * x1.x, -2.f * x1.y);
+  }
+}
+
+template <int M, int THREADS>
+__device__ __forceinline__ void c2r_issue_early(const TileIO& io, C2REarlyLoads<M, THREADS>& r) {
+  static_for<C2REarlyLoads<M, THREADS>::kEarly>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const int it = threadIdx.x + i * THREADS;
+    if (it < (M / 2 + 1) * 8) c2r_load_pair<M>(io, it, r.A[i], r.B[i]);
+  });
+}
+
+// Merge a tile whose early loads are in r; ends with the barrier before the first pass.
+template <int M, int THREADS>
+__device__ __forceinline__ void c2r_merge_rest(float2* sm, const float2* tw2, float interior, const TileIO& io,
+                                               const C2REarlyLoads<M, THREADS>& r) {
+  using E = C2REarlyLoads<M, THREADS>;
+  constexpr int NPAIR = M / 2 + 1;
+  static_for<E::kIters - E::kEarly>([&](auto ic) {
+    constexpr int i = decltype(ic)::value + E::kEarly;
+    const int it = threadIdx.x + i * THREADS;
+    if (it < NPAIR * 8) {
+      float4 a, c;
+      c2r_load_pair<M>(io, it, a, c);
+      c2r_merge_pair_to<M>(sm, tw2, interior, it, a, c);
+    }
+  });
+  static_for<E::kEarly>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const int it = threadIdx.x + i * THREADS;
+    if (it < NPAIR * 8) c2r_merge_pair_to<M>(sm, tw2, interior, it, r.A[i], r.B[i]);
+  });
+  __syncthreads();
+}
+
 // The column-side load of bins 0..M fused with the C2R merge: the pair
 // (k, M-k) is read from global memory and merged into rows k and M-k of the
 // tile, with the arithmetic of c2r_pre. Full, aligned tiles read two pencils

@@ -94,6 +94,37 @@ __global__ void __launch_bounds__(stage_threads(L, PREC), stage_min_blocks(L, PR
   load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre || KIND >= kPoissonZB);
   __syncthreads();
   pdl_wait_prev();
+  if constexpr (stage_loops(L) && KIND == kC2RPre && PREC == kPrecFP32) {
+    if (d.in_mode == kCol && static_cast<const void*>(d.in) != static_cast<const void*>(d.out)) {
+      // C2R from the column side: the first loads of the block's next tile are
+      // issued before this tile's row store, so their latency overlaps the store
+      C2REarlyLoads<L, THREADS> r;
+      bool have = false;  // r holds the early loads of `tile`
+      for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
+        int o, g0;
+        const TileIO io = make_io(d, tile, o, g0);
+        if (pair_vec_ok(io.gin, io.in_n, io.valid)) {
+          if (!have) c2r_issue_early<L, THREADS>(io, r);
+          c2r_merge_rest<L, THREADS>(sm, tw2, d.interior, io, r);
+        } else {
+          col_load_c2r_pre<L, THREADS>(sm, tw2, d.interior, io);
+        }
+        fft_passes<L, +1, THREADS, false, false, false>(sm, tw, io);
+        have = false;
+        const long long next = tile + gridDim.x;
+        if (next < d.n_tiles) {
+          const TileIO nio = make_io(d, next, o, g0);
+          if (pair_vec_ok(nio.gin, nio.in_n, nio.valid)) {
+            c2r_issue_early<L, THREADS>(nio, r);
+            have = true;
+          }
+        }
+        row_store<THREADS, L>(sm, io);
+        __syncthreads();
+      }
+      return;
+    }
+  }
   if constexpr (stage_loops(L)) {
     for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) {
       process_tile<L, DIR, KIND, THREADS, PREC>(d, tile, sm, tw, tw2);
