@@ -96,6 +96,8 @@ typedef struct gbfft_plan_s* gbfft_plan;
 #define GBFFT_ERR_TIMEOUT (-7)          /* a device dependency wait ran out of time */
 #define GBFFT_ERR_NO_DEVICE (-8)        /* no CUDA device */
 #define GBFFT_ERR_STATIC_LIMIT (-9)     /* grid larger than GBFFT_NOALLOC_MAX_POINTS */
+#define GBFFT_ERR_SETUP_IN_CAPTURE (-10) /* gbfft_exec_c2c_noalloc: a device's first call came while its
+                                            stream was capturing (set-up needs a synchronous copy) */
 
 /*
  * Create a plan for `batch` grids of nx x ny x nz (Section V-B: a reusable
@@ -275,9 +277,9 @@ int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* 
 /*
  * Allocation-free C2C transform (the paper has no counterpart; this entry
  * point exists for callers that cannot allocate device memory when they run
- * the transform -- for example code that runs while a CUDA graph is being
- * captured, or code whose device memory belongs to a pool or framework
- * allocator that forbids side allocations). It needs no plan and calls no
+ * the transform -- code whose device memory belongs to a pool or framework
+ * allocator that forbids side allocations, or latency-critical loops in
+ * which a cudaMalloc would synchronise the device). It needs no plan and calls no
  * cudaMalloc, cudaFree or other allocating routine: the intermediate stage
  * array lives in a file-scope static __device__ buffer of
  * GBFFT_NOALLOC_MAX_POINTS complex64 values (32 MiB) that every GPU which
@@ -293,7 +295,11 @@ int gbfft_debug_run(gbfft_plan plan, int step, const void* in, void* out, void* 
  *                pencil x, y, z stages) and returns without waiting
  * The first call on a device sets that device up (resolves the static
  * arrays' device addresses, uploads the twiddle tables with a synchronous
- * copy); make that first call before any stream capture. Every call shares
+ * copy); make that first call before any stream capture: if `stream` is
+ * capturing at that point the call returns GBFFT_ERR_SETUP_IN_CAPTURE and
+ * enqueues nothing. Later calls take no lock. Every stage's read and write
+ * extents are checked on the host before anything is launched
+ * (GBFFT_ERR_INVALID_ARG). Every call shares
  * the one scratch buffer: calls that overlap on the GPU (different streams,
  * or concurrent host threads) race on it. Nothing in it needs to start at
  * zero -- each stage writes every element before the next reads it.

@@ -44,6 +44,7 @@ GBFFT_ERR_CUDA = -6
 GBFFT_ERR_TIMEOUT = -7
 GBFFT_ERR_NO_DEVICE = -8
 GBFFT_ERR_STATIC_LIMIT = -9
+GBFFT_ERR_SETUP_IN_CAPTURE = -10
 GBFFT_NOALLOC_MAX_POINTS = 4194304
 
 # every symbol include/gbfft.h declares

@@ -1018,6 +1018,8 @@ const char* gbfft_strerror(int code) {
       return "no CUDA device";
     case GBFFT_ERR_STATIC_LIMIT:
       return "grid larger than the static scratch of gbfft_exec_c2c_noalloc";
+    case GBFFT_ERR_SETUP_IN_CAPTURE:
+      return "gbfft_exec_c2c_noalloc: first call on this device made while its stream was capturing";
     default:
       return "unknown error";
   }

@@ -1,12 +1,11 @@
 // Allocation-free entry point: gbfft_exec_c2c_noalloc (see include/gbfft.h).
 //
 // Some callers cannot allocate device memory at the moment they need a
-// transform: code that runs while a CUDA graph is being captured (cudaMalloc
-// is not a capturable operation and would break the capture), callers whose
-// memory is owned by a custom pool or framework allocator that forbids
-// side allocations, and latency-critical loops where a cudaMalloc would
-// synchronise the device. A gbfft_plan allocates twiddle tables, schedules and
-// workspace, so those callers cannot create one at that point.
+// transform: callers whose device memory is owned by a custom pool or
+// framework allocator that forbids side allocations, and latency-critical
+// loops where a cudaMalloc would synchronise the device. A gbfft_plan
+// allocates twiddle tables, schedules and workspace, so those callers cannot
+// create one at that point.
 //
 // This entry point runs the same stage kernels as the pencil C2C path
 // (staged launches), with the intermediate stage buffer in a file-scope
@@ -15,6 +14,7 @@
 // every GPU that loads the library, for as long as it stays loaded.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -45,7 +45,7 @@ constexpr int kMaxLen = 1024;
 constexpr int kMaxDevices = 64;
 
 struct DeviceState {
-  bool ready = false;
+  std::atomic<bool> ready{false};  // set once, with release order, after the fields below
   float2* scratch = nullptr;   // device address of g_noalloc_scratch on this device
   float2* tw = nullptr;        // device address of g_noalloc_twiddles on this device
   int tw_offset[kMaxLen + 1];  // offset of the W_L table, -1 if L unsupported
@@ -56,10 +56,23 @@ DeviceState g_state[kMaxDevices];
 
 // Set-up, once per device, with that device current: resolve the two arrays'
 // device addresses and upload the twiddle tables (FP64 cos/sin, rounded once).
-int setup_device(int dev, DeviceState** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
+// A device that is ready is found without taking the lock. The upload is a
+// synchronous copy, which a stream capture in progress on `stream` would not
+// survive, so set-up is refused (nothing enqueued) while `stream` captures.
+int setup_device(int dev, cudaStream_t stream, DeviceState** out) {
   DeviceState& st = g_state[dev];
-  if (st.ready) {
+  if (st.ready.load(std::memory_order_acquire)) {
+    *out = &st;
+    return GBFFT_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return GBFFT_ERR_CUDA;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return GBFFT_ERR_SETUP_IN_CAPTURE;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (st.ready.load(std::memory_order_acquire)) {
     *out = &st;
     return GBFFT_OK;
   }
@@ -81,7 +94,7 @@ int setup_device(int dev, DeviceState** out) {
   }
   if (cudaMemcpyToSymbol(g_noalloc_twiddles, host.data(), host.size() * sizeof(float2)) != cudaSuccess)
     return GBFFT_ERR_CUDA;
-  st.ready = true;
+  st.ready.store(true, std::memory_order_release);
   *out = &st;
   return GBFFT_OK;
 }
@@ -120,6 +133,16 @@ StageDesc stage(const void* in, void* out, int L, int dir, int n_outer, int n_gr
   return d;
 }
 
+// Largest float2 offset + 1 a stage reads / writes (one grid, positive strides).
+long long read_end(const StageDesc& d) {
+  return (long long)(d.n_outer - 1) * d.in_o + (long long)(d.n_group - 1) * d.in_g + (long long)(d.n_in - 1) * d.in_n +
+         1;
+}
+long long write_end(const StageDesc& d) {
+  return (long long)(d.n_outer - 1) * d.out_o + (long long)(d.n_group - 1) * d.out_g +
+         (long long)(d.n_out - 1) * d.out_n + 1;
+}
+
 }  // namespace
 
 extern "C" int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void* in, void* out, void* stream) {
@@ -135,14 +158,14 @@ extern "C" int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void
     return GBFFT_ERR_UNSUPPORTED_SIZE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GBFFT_ERR_NO_DEVICE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   DeviceState* st = nullptr;
-  int rc = setup_device(dev, &st);
+  int rc = setup_device(dev, s, &st);
   if (rc) return rc;
   const float2* twx = st->tw + st->tw_offset[nx];
   const float2* twy = st->tw + st->tw_offset[ny];
   const float2* twz = st->tw + st->tw_offset[nz];
   float2* W = st->scratch;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const float invN = (float)(1.0 / (double)n);
   // Layouts: A natural [z][y][x]; B [z][x][y]; C [x][y][z]. Every element of
   // the scratch is written by one stage before the next stage reads it, so
@@ -165,6 +188,11 @@ extern "C" int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void
     st3[2] = stage(W, out, nx, +1, nz, ny, (long long)nx * ny, 1, ny, kCol, (long long)nx * ny, nx, 1, kRow, sc, twx,
                    n);
   }
+  // Host-side bounds check before anything is launched: in, out and the
+  // scratch each hold n points (the scratch more), so every stage's largest
+  // read and write offset must stay below n.
+  for (int k = 0; k < 3; ++k)
+    if (read_end(st3[k]) > n || write_end(st3[k]) > n) return GBFFT_ERR_INVALID_ARG;
   for (int k = 0; k < 3; ++k) {
     rc = launch_stage_external(st3[k], s);
     if (rc) return rc;

@@ -56,36 +56,47 @@ def test_batched_small_mixed(gb):
 
 
 def test_config4_64_uneven_grids_graph_replay(gb):
-    """Config 4: 64 grids, one persistent launch captured in a CUDA graph and replayed."""
+    """Config 4: 64 grids, one persistent launch captured in a CUDA graph and replayed, forward
+    and inverse; every grid of both directions against the FP64 oracle."""
     from paper_2601_12209_gb300 import abi
     shapes, grids = synth.batched_grids(64, seed=6)
     m = gb.ManyPlan(shapes)
     x = m.pack([g.cuda() for g in grids])
     y = m.empty()
+    z = m.empty()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=s)  # warm-up outside capture
+        m.exec(abi.GBFFT_OP_INVERSE, x, z, stream=s)
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        m.exec(abi.GBFFT_OP_FORWARD, x, y)
+    graphs = {}
+    for op, out in ((abi.GBFFT_OP_FORWARD, y), (abi.GBFFT_OP_INVERSE, z)):
+        graphs[op] = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graphs[op]):
+            m.exec(op, x, out)
     y.zero_()
-    graph.replay()
+    z.zero_()
+    graphs[abi.GBFFT_OP_FORWARD].replay()
+    graphs[abi.GBFFT_OP_INVERSE].replay()
     torch.cuda.synchronize()
     assert m.device_error() == 0
-    outs = m.unpack(y)
-    rng = np.random.default_rng(0)
-    for i in sorted(rng.choice(64, size=12, replace=False).tolist()) + [0, 63]:
-        e = oracle.rel_l2(outs[i].cpu().numpy(), oracle.fft3(grids[i].numpy()))
-        print(f"[batched] cfg4 grid {i} {shapes[i]}: rel-L2 {e:.3e}")
-        assert e < TOL
+    fwd, inv = m.unpack(y), m.unpack(z)
+    worst = [0.0, 0.0]
+    for i in range(64):
+        g = grids[i].numpy()
+        e = oracle.rel_l2(fwd[i].cpu().numpy(), oracle.fft3(g))
+        e2 = oracle.rel_l2(inv[i].cpu().numpy(), oracle.ifft3(g))
+        print(f"[batched] cfg4 grid {i} {shapes[i]}: fwd rel-L2 {e:.3e}, inv rel-L2 {e2:.3e}")
+        worst = [max(worst[0], e), max(worst[1], e2)]
+        assert e < TOL and e2 < TOL
+    print(f"[batched] cfg4 worst over 64 grids: fwd {worst[0]:.3e}, inv {worst[1]:.3e}")
     # a second replay after the input changed in place
     grids2 = [torch.conj_physical(g) for g in grids[:4]]
     for g, off, (nx, ny, nz) in zip(grids2, m.offsets, shapes):
         x[off:off + nx * ny * nz].copy_(g.reshape(-1).cuda())
-    graph.replay()
+    graphs[abi.GBFFT_OP_FORWARD].replay()
     torch.cuda.synchronize()
     for i in range(4):
         e = oracle.rel_l2(m.unpack(y)[i].cpu().numpy(), oracle.fft3(grids2[i].numpy()))

@@ -1,6 +1,7 @@
-"""Full-size parity at the benchmark's sizes, in the launch configuration the
-benchmark times (persistent pencil launch, and the slab variant): every
-output element against the FP64 oracle, plus direct triple-sum DFT samples.
+"""Full-size parity at the benchmark's sizes, in the launch configurations the
+benchmark times (the autotuned pencil plan it publishes, the persistent and
+staged pencil launches, the slab variant): every output element against the
+FP64 oracle, plus direct triple-sum DFT samples.
 """
 import numpy as np
 import pytest
@@ -30,13 +31,21 @@ def err(name, got, ref):
     return e
 
 
-@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+def _tuned(plan, mode):
+    """The autotuned plan is the one the benchmark times: tune it the same way."""
+    if mode == "pencil_tuned":
+        tuning = plan.autotune()
+        print(f"[parity-full] tuning {tuning}")
+
+
+@pytest.mark.parametrize("mode", ["pencil_tuned", "pencil", "pencil_staged", "slab"])
 def test_r2c_c2r_512(gb, mode):
     """Config: R2C forward and C2R inverse at 512^3 FP32, real N(0,1) input."""
     n = 512
     slab = mode == "slab"
     r = synth.normal_real((n, n, n), seed=2)
     plan = gb.Plan(n, n, n, kind="r2c", slab=slab, staged=(mode == "pencil_staged"))
+    _tuned(plan, mode)
     rd = r.cuda()
     H = plan.forward(rd)
     r2 = plan.inverse(H)
@@ -55,13 +64,14 @@ def test_r2c_c2r_512(gb, mode):
     assert err(f"r2c 512 roundtrip {mode}", r2.cpu().numpy(), r.numpy()) < TOL
 
 
-@pytest.mark.parametrize("mode", ["pencil", "pencil_staged", "slab"])
+@pytest.mark.parametrize("mode", ["pencil_tuned", "pencil", "pencil_staged", "slab"])
 def test_c2c_512(gb, mode):
     """C2C forward+inverse at 512^3, complex64 uniform[-1,1] (the headline C2C configuration)."""
     n = 512
     slab = mode == "slab"
     x = synth.uniform_complex((n, n, n), seed=3)
     plan = gb.Plan(n, n, n, slab=slab, staged=(mode == "pencil_staged"))
+    _tuned(plan, mode)
     X = plan.forward(x.cuda())
     torch.cuda.synchronize()
     Xh = X.cpu().numpy()

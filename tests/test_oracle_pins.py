@@ -375,3 +375,39 @@ def test_dst_z_and_r2r_z_round_trip():
     ref = np.zeros_like(Y)
     ref[kz, ky, kx] = nz * nx * ny
     np.testing.assert_allclose(Y, ref, atol=1e-10)
+
+
+@pytest.mark.parametrize("kinds", [("dct", None, None), (None, "dct", None), ("dst", None, None), (None, "dst", None),
+                                   ("dst", "dct", None), ("dct", "dst", "dst"), ("dct", "dct", "dct")],
+                         ids=lambda k: "-".join(str(v) for v in k))
+def test_r2r_x_and_y_axes_against_library(kinds):
+    """The per-axis mixed transform with DCT / DST on the x and y axes: every R2R axis against
+    scipy.fft's dct / dst (an independent library; types II forward, III inverse), every Fourier
+    axis against numpy.fft, forward unscaled and inverse scaled by prod(2n R2R, n DFT)."""
+    sf = pytest.importorskip("scipy.fft")
+    kx, ky, kz = kinds
+    c = synth.uniform_complex((5, 6, 8), seed=37).numpy().astype(np.complex128)
+    fwd = c
+    for axis, k in ((-1, kx), (-2, ky), (-3, kz)):
+        fwd = np.fft.fft(fwd, axis=axis) if k is None else \
+            (sf.dct if k == "dct" else sf.dst)(fwd, type=2, axis=axis)
+    np.testing.assert_allclose(oracle.r2r(c, kinds), fwd, atol=1e-11)
+    inv = c
+    for axis, k in ((-3, kz), (-2, ky), (-1, kx)):
+        inv = np.fft.ifft(inv, axis=axis) if k is None else \
+            (sf.dct if k == "dct" else sf.dst)(inv, type=3, axis=axis) / (2 * c.shape[axis])
+    np.testing.assert_allclose(oracle.r2r(c, kinds, inverse=True), inv, atol=1e-12)
+
+
+def test_r2r_y_axis_of_real_input_against_library():
+    """Real input with the x axis Fourier (R2C, bins 0..nx/2) and R2R along y and z: numpy.fft.rfft
+    along x, scipy.fft dct / dst along y and z; the inverse with nx given returns the real grid."""
+    sf = pytest.importorskip("scipy.fft")
+    r = synth.normal_real((4, 6, 10), seed=38).numpy().astype(np.float64)
+    for ky, kz in (("dct", None), ("dst", "dct"), ("dct", "dst")):
+        ref = np.fft.rfft(r, axis=-1)
+        ref = (sf.dct if ky == "dct" else sf.dst)(ref, type=2, axis=-2)
+        ref = np.fft.fft(ref, axis=-3) if kz is None else (sf.dct if kz == "dct" else sf.dst)(ref, type=2, axis=-3)
+        got = oracle.r2r(r, (None, ky, kz))
+        np.testing.assert_allclose(got, ref, atol=1e-11)
+        np.testing.assert_allclose(oracle.r2r(got, (None, ky, kz), inverse=True, nx=10), r, atol=1e-12)
