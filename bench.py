@@ -73,7 +73,8 @@ def measured_peaks():
 
 
 # the sources of the stage, tensor-copy and warp-per-pencil kernels' device code
-KERNEL_SOURCES = ("gbfft_internal.h", "gbfft_device.cuh", "gbfft_kernels.cuh", "gbfft_tma.cuh", "gbfft_warp.cuh")
+KERNEL_SOURCES = ("gbfft_internal.h", "gbfft_device.cuh", "gbfft_kernels.cuh", "gbfft_tma.cuh", "gbfft_warp.cuh",
+                  "gbfft_prefetch.cuh")
 # ... and of the fused plane kernels
 PLANE_SOURCES = KERNEL_SOURCES + ("gbfft_plane.cuh",)
 
@@ -409,7 +410,8 @@ def main():
             axes = ("x", "y", "z") if name == "forward" else ("z", "y", "x")
             for k, t in enumerate(seg):
                 # the warp kernel serves the complex length-512 stages (y, z), not the real x stages
-                kern = ("warp_stage_kernel" if (tune["tma_mask"] >> (20 + k)) & 1 and axes[k] != "x" else
+                kern = ("c2r_prefetch_kernel" if k < 4 and (tune["tma_mask"] >> (28 + k)) & 1 else
+                        "warp_stage_kernel" if (tune["tma_mask"] >> (20 + k)) & 1 and axes[k] != "x" else
                         "tma_stage_kernel" if (tune["tma_mask"] >> k) & 1 else "stage_kernel")
                 segs.append((f"{name} stage {axes[k]} {kern}", t, stage_bytes[k]))
     dom = max(segs, key=lambda x: x[1])
@@ -514,7 +516,8 @@ def ncu_case(name):
 
 
 def batched_variant(torch, gb, abi, stream, steps, warmup):
-    """64 uneven C2C grids: one graph-captured batched launch vs one plan per grid (forward)."""
+    """64 uneven C2C grids (forward): the graph-captured one launch with one 16-pencil tile per
+    ticket, then the tile-shape autotuner's choice in all three schedules."""
     import synth
     shapes, grids = synth.batched_grids(64, seed=6)
     m = gb.ManyPlan(shapes)
@@ -523,23 +526,10 @@ def batched_variant(torch, gb, abi, stream, steps, warmup):
     npts = sum(nx * ny * nz for (nx, ny, nz) in shapes)
     flops = sum(flops_5n(*s) for s in shapes)
     alg_bytes = 48 * npts
-    with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
-            m.exec_separate(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
-    graph3 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph3, stream=stream):
-        m.exec_staged(abi.GBFFT_OP_FORWARD, x, y, stream=stream)
-    res = {"grids": 64, "points": npts, "largest_smallest_ratio": max(a * b * c for a, b, c in shapes)
-           / min(a * b * c for a, b, c in shapes)}
-    for name, fn in (("one_launch_graph", lambda: graph.replay()),
-                     ("stage_launches_graph", lambda: graph3.replay()),
-                     ("one_launch", lambda: m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)),
-                     ("separate_plans", lambda: m.exec_separate(abi.GBFFT_OP_FORWARD, x, y, stream=stream))):
+    res = {"grids": 64, "points": npts, "alg_bytes": alg_bytes,
+           "largest_smallest_ratio": max(a * b * c for a, b, c in shapes) / min(a * b * c for a, b, c in shapes)}
+
+    def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -550,7 +540,29 @@ def batched_variant(torch, gb, abi, stream, steps, warmup):
             e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        res[name] = {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9}
+        return {"ms": ms, "gflops": flops / (ms * 1e-3) / 1e9, "alg_gbs": alg_bytes / (ms * 1e-3) / 1e9}
+
+    def graph_of(fn):
+        with torch.cuda.stream(stream):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        return g
+
+    one = lambda: m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=stream)  # noqa: E731
+    g1 = graph_of(one)
+    res["one_launch_graph_one_tile_per_ticket"] = timed(lambda: g1.replay())
+    del g1
+    res["tuning"] = {k: {"tiles_per_ticket": v["teams"], "ms": v["ms"]} for k, v in m.autotune(stream).items()}
+    graph = graph_of(one)
+    graph3 = graph_of(lambda: m.exec_staged(abi.GBFFT_OP_FORWARD, x, y, stream=stream))
+    for name, fn in (("one_launch_graph", lambda: graph.replay()),
+                     ("stage_launches_graph", lambda: graph3.replay()),
+                     ("one_launch", one),
+                     ("separate_plans", lambda: m.exec_separate(abi.GBFFT_OP_FORWARD, x, y, stream=stream))):
+        res[name] = timed(fn)
     res["device_error"] = m.device_error()
     m.close()
     return res

@@ -309,18 +309,20 @@ int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void* in, void*
 
 /*
  * Batched grids (the paper's task graph over many chunks of uneven cost,
- * Sections III-C and IV-D, Table II): `count` C2C FP32 grids of different
- * sizes (dims[3g..3g+2] = nx, ny, nz of grid g; each length 2^a 3^b 5^c in
+ * Sections III-C and IV-D, Table II): `count` grids of different sizes
+ * (dims[3g..3g+2] = nx, ny, nz of grid g; each length 2^a 3^b 5^c in
  * 32..256) transformed by ONE persistent launch whose blocks take the tiles of
- * every grid from one ticket counter (stage-major across grids, bounded
- * per-grid dependency waits). The grids are packed back to back in `in` and
- * `out` (grid g starts at element offset gbfft_many_layout(g); every grid
- * starts 16-byte aligned). The launch needs only in/out and plan-owned
- * memory, so it can be captured in a CUDA graph and replayed. count <= 85.
- * flags: 0 or GBFFT_DEBUG_TIMEOUT.
+ * every grid from one ticket counter (bounded per-grid dependency waits). The
+ * grids are packed back to back in `in` and `out` (grid g starts at element
+ * offset gbfft_many_layout(g); every grid starts 16-byte aligned). The launch
+ * needs only in/out and plan-owned memory, so it can be captured in a CUDA
+ * graph and replayed. count <= 85.
+ *   kind, dtype : as in gbfft_plan_create; batching is built for GBFFT_C2C with
+ *                 GBFFT_FP32 only (any other combination: GBFFT_ERR_INVALID_ARG)
+ *   flags       : 0 or GBFFT_DEBUG_TIMEOUT
  */
 typedef struct gbfft_many_s* gbfft_many;
-int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flags);
+int gbfft_many_create(gbfft_many* out, int count, const int* dims, int kind, int dtype, unsigned flags);
 /* Element offset of grid `grid` and the total complex elements of the packed buffers. */
 int gbfft_many_layout(gbfft_many m, int grid, long long* offset, long long* total);
 /* One persistent launch for all grids; op GBFFT_OP_FORWARD or GBFFT_OP_INVERSE (1/N per grid). */
@@ -330,6 +332,24 @@ int gbfft_many_exec(gbfft_many m, int op, const void* in, void* out, void* strea
 int gbfft_many_exec_staged(gbfft_many m, int op, const void* in, void* out, void* stream);
 /* The same transforms as one plan per grid, launched one after another (for comparison). */
 int gbfft_many_exec_separate(gbfft_many m, int op, const void* in, void* out, void* stream);
+/*
+ * Tile-shape autotuner of the batched plan (Section III-C: the granularity of
+ * a task against its scheduling overhead; Section V-B: plans tuned per size).
+ * A ticket of the one launch carries S = 1, 2 or 4 tiles of 16 pencils, run
+ * side by side by teams of 256 / S threads: 16 S pencils per block and 16 / S
+ * threads per pencil, which fills the block at the short lengths. For each
+ * pipeline (0 forward, 1 inverse) and each distinct axis length the tuner
+ * times the one-launch schedule on `stream` (CUDA events) for every S the
+ * length allows and keeps the fastest (coordinate descent, two sweeps);
+ * the per-stage launches use the same choice. Blocking; allocates two scratch
+ * buffers of the packed size while it runs; not during stream capture.
+ */
+int gbfft_many_autotune(gbfft_many m, void* stream);
+/* The tiles per ticket of pipeline 0/1: lengths[i], teams[i] for i < min(*n, cap); *n receives the
+   number of distinct lengths; *ms (may be NULL) the tuned one-launch time (0 if not tuned). */
+int gbfft_many_get_tuning(gbfft_many m, int pipeline, int* lengths, int* teams, int cap, int* n, float* ms);
+/* Set tiles per ticket by hand (teams 1, 2 or 4, at most what the length allows; synchronous upload). */
+int gbfft_many_set_tuning(gbfft_many m, int pipeline, const int* lengths, const int* teams, int n);
 /* Read and clear the device error word of the batched launches (synchronises). */
 int gbfft_many_get_device_error(gbfft_many m, int* code);
 void gbfft_many_destroy(gbfft_many m);

@@ -254,6 +254,17 @@ class ManyPlan:
         abi.gbfft_many_exec_separate(self.handle, int(op), x.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
+    def autotune(self, stream=None) -> dict:
+        """Pick the tiles per ticket of every axis length for both directions (times the one launch)."""
+        abi.gbfft_many_autotune(self.handle, _stream_handle(stream))
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        return {name: abi.gbfft_many_get_tuning(self.handle, k) for k, name in enumerate(("forward", "inverse"))}
+
+    def set_tuning(self, pipeline: int, teams: dict) -> None:
+        abi.gbfft_many_set_tuning(self.handle, pipeline, teams)
+
     def device_error(self) -> int:
         return abi.gbfft_many_get_device_error(self.handle)
 

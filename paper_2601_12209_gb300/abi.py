@@ -57,6 +57,7 @@ EXPORTED = (
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
     "gbfft_plan_set_tuning", "gbfft_many_create", "gbfft_many_layout", "gbfft_many_exec",
     "gbfft_many_exec_separate", "gbfft_many_get_device_error", "gbfft_many_destroy", "gbfft_many_exec_staged",
+    "gbfft_many_autotune", "gbfft_many_get_tuning", "gbfft_many_set_tuning",
 )
 
 _lib = None
@@ -110,7 +111,11 @@ def load() -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
             "gbfft_plan_time_stages": (i, [vp, i]),
             "gbfft_plan_set_tuning": (i, [vp, i, i, u]),
-            "gbfft_many_create": (i, [plan_p, i, ctypes.POINTER(i), u]),
+            "gbfft_many_create": (i, [plan_p, i, ctypes.POINTER(i), i, i, u]),
+            "gbfft_many_autotune": (i, [vp, vp]),
+            "gbfft_many_get_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), i, ctypes.POINTER(i),
+                                          ctypes.POINTER(ctypes.c_float)]),
+            "gbfft_many_set_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), i]),
             "gbfft_many_layout": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
             "gbfft_many_exec": (i, [vp, i, vp, vp, vp]),
             "gbfft_many_exec_separate": (i, [vp, i, vp, vp, vp]),
@@ -284,12 +289,34 @@ def gbfft_plan_stage_times(plan: int, pipeline: int) -> tuple[list[float], int]:
     return [avg[k] for k in range(nseg.value)], ncalls.value
 
 
-def gbfft_many_create(shapes, flags: int = 0) -> int:
+def gbfft_many_create(shapes, flags: int = 0, kind: int = GBFFT_C2C, dtype: int = GBFFT_FP32) -> int:
     """shapes: list of (nx, ny, nz)."""
     dims = (ctypes.c_int * (3 * len(shapes)))(*[int(v) for sh in shapes for v in sh])
     h = ctypes.c_void_p()
-    _call("gbfft_many_create", ctypes.byref(h), len(shapes), dims, int(flags))
+    _call("gbfft_many_create", ctypes.byref(h), len(shapes), dims, int(kind), int(dtype), int(flags))
     return h.value
+
+
+def gbfft_many_autotune(m: int, stream: int = 0) -> None:
+    _call("gbfft_many_autotune", ctypes.c_void_p(m), ctypes.c_void_p(stream))
+
+
+def gbfft_many_get_tuning(m: int, pipeline: int) -> dict:
+    """{"teams": {length: tiles per ticket}, "ms": tuned one-launch time (0 if untuned)}."""
+    cap = 64
+    lens, teams = (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+    n, ms = ctypes.c_int(), ctypes.c_float()
+    _call("gbfft_many_get_tuning", ctypes.c_void_p(m), int(pipeline), lens, teams, cap, ctypes.byref(n),
+          ctypes.byref(ms))
+    return {"teams": {int(lens[i]): int(teams[i]) for i in range(min(n.value, cap))}, "ms": ms.value}
+
+
+def gbfft_many_set_tuning(m: int, pipeline: int, teams: dict) -> None:
+    """teams: {length: tiles per ticket (1, 2 or 4)}."""
+    n = len(teams)
+    lens = (ctypes.c_int * max(n, 1))(*[int(k) for k in teams])
+    ts = (ctypes.c_int * max(n, 1))(*[int(v) for v in teams.values()])
+    _call("gbfft_many_set_tuning", ctypes.c_void_p(m), int(pipeline), lens, ts, n)
 
 
 def gbfft_many_layout(m: int, grid: int) -> tuple[int, int]:

@@ -17,6 +17,7 @@
 #include "gbfft_kernels.cuh"
 #include "gbfft_many.cuh"
 #include "gbfft_plane.cuh"
+#include "gbfft_prefetch.cuh"
 #include "gbfft_warp.cuh"
 
 namespace gbfft {
@@ -40,6 +41,12 @@ void register_tma_group_1(std::vector<TmaKernel>&);
 void register_tma_group_2(std::vector<TmaKernel>&);
 void register_plane_group_0(std::vector<PlaneKernel>&);
 void register_warp_group_0(std::vector<WarpKernel>&);
+void register_prefetch_group_0(std::vector<PrefetchKernel>&);
+
+std::vector<PrefetchKernel>& prefetch_registry() {
+  static std::vector<PrefetchKernel> v;
+  return v;
+}
 
 std::vector<WarpKernel>& warp_registry() {
   static std::vector<WarpKernel> v;
@@ -87,6 +94,7 @@ static void ensure_registry() {
     register_tma_group_2(t);
     register_plane_group_0(plane_registry());
     register_warp_group_0(warp_registry());
+    register_prefetch_group_0(prefetch_registry());
   });
 }
 
@@ -284,6 +292,7 @@ struct gbfft_plan_s {
     unsigned tma_mask = 0;  // bit s: stage s uses the tensor-copy kernel
     unsigned plane_mask = 0;  // bit s: stages s and s+1 run as one fused plane launch
     unsigned warp_mask = 0;   // bit s: stage s runs the warp-per-pencil kernel
+    unsigned prefetch_mask = 0;  // bit s: stage s runs the cp.async prefetch C2R kernel
     int plane_cx = 0;         // CTAs per plane cluster of the fused launches (0: by plane size)
     float ms = 0.f;         // measured time of the chosen launch(es)
     float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -615,6 +624,20 @@ static cudaError_t launch_stage_kernel(const void* fn, long long grid, int threa
 // is built (lengths 512 and 256 complex, the length-256 real x stages; FP32).
 constexpr unsigned kUseWarpKernel = 1u << 30;
 
+// Internal launch flag: run a C2R x stage with the cp.async prefetch kernel
+// (column-side half spectrum in, real rows out; FP32).
+constexpr unsigned kUsePrefetchKernel = 1u << 29;
+
+static const PrefetchKernel* find_prefetch(const StageDesc& d) {
+  if (d.prec != kPrecFP32 || d.kind != kC2RPre || d.dir < 0 || !d.tw2) return nullptr;
+  if (d.in_mode != kCol || d.out_mode != kRow || static_cast<const void*>(d.in) == static_cast<const void*>(d.out))
+    return nullptr;
+  ensure_registry();
+  for (const auto& k : prefetch_registry())
+    if (k.L == d.L) return &k;
+  return nullptr;
+}
+
 static const WarpKernel* find_warp(const StageDesc& d) {
   if (d.prec != kPrecFP32 || !d.twn) return nullptr;
   if (d.kind != kPlain && d.kind != kR2CPost && d.kind != kC2RPre) return nullptr;
@@ -668,6 +691,17 @@ static void merge_pencils(StageDesc& d) {
 // described by a tensor map, else the load/store kernel.
 static int launch_stage(const StageDesc& d, cudaStream_t stream, unsigned flags = 0, int* err = nullptr) {
   if (d.n_tiles == 0) return GBFFT_OK;
+  if (flags & kUsePrefetchKernel) {
+    if (const PrefetchKernel* pk = find_prefetch(d)) {
+      int bpsm = 1;
+      cudaError_t e = launch_info(pk->fn, pk->threads, pk->smem, &bpsm);
+      if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+      const long long grid = std::min<long long>(d.n_tiles, (long long)sm_count() * bpsm);
+      StageDesc dd = d;
+      void* args[] = {&dd};
+      return cuda_err(launch_stage_kernel(pk->fn, grid, pk->threads, args, pk->smem, stream));
+    }
+  }
   if (flags & kUseWarpKernel) {
     if (const WarpKernel* wk = find_warp(d)) {
       int bpsm = 1;
@@ -833,7 +867,7 @@ static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDes
 // tensor-copy kernel for stage s when it can run there; bit s of plane_mask:
 // stages s and s+1 as one fused plane launch when they form an in-plane pair).
 static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe,
-                      unsigned plane_mask = 0, int plane_cx = 0, unsigned warp_mask = 0) {
+                      unsigned plane_mask = 0, int plane_cx = 0, unsigned warp_mask = 0, unsigned prefetch_mask = 0) {
   record_event(p, stream, pipe, true);
   for (int s = 0; s < P.n; ++s) {
     if ((plane_mask >> s) & 1u) {
@@ -845,7 +879,8 @@ static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cud
         continue;
       }
     }
-    const unsigned f = (((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA) | (((warp_mask >> s) & 1u) ? kUseWarpKernel : 0u);
+    const unsigned f = (((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA) | (((warp_mask >> s) & 1u) ? kUseWarpKernel : 0u) |
+                       (((prefetch_mask >> s) & 1u) ? kUsePrefetchKernel : 0u);
     int rc = launch_stage(P.st[s], stream, f, &p->ctl->error);
     if (rc) return rc;
     record_event(p, stream, pipe, false);
@@ -865,7 +900,7 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
       return rc;
     }
     const gbfft_plan_s::Tuning& t = p->tune[pipe];
-    return run_staged(p, P, t.tma_mask, stream, pipe, t.plane_mask, t.plane_cx, t.warp_mask);
+    return run_staged(p, P, t.tma_mask, stream, pipe, t.plane_mask, t.plane_cx, t.warp_mask, t.prefetch_mask);
   }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
   const unsigned tm = (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu;
@@ -1432,6 +1467,16 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
           t.warp_mask |= 1u << s;
         }
       }
+      if (s < 4 && find_prefetch(d)) {
+        float tq = time_calls(
+            [&] { return launch_stage(d, st, GBFFT_NO_TMA | kUsePrefetchKernel, &plan->ctl->error); }, st, reps);
+        if (tq >= 0.f && tq < best) {
+          best = tq;
+          t.tma_mask &= ~(1u << s);
+          t.warp_mask &= ~(1u << s);
+          t.prefetch_mask |= 1u << s;
+        }
+      }
       t.stage_ms[s] = best;
       staged_ms += best;
     }
@@ -1448,8 +1493,9 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
     if (pm) {
       const unsigned tm = t.tma_mask;
       const unsigned wm = t.warp_mask;
+      const unsigned qm = t.prefetch_mask;
       for (int cx : {2, 4, 8}) {
-        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx, wm); }, st, reps);
+        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx, wm, qm); }, st, reps);
         if (tf >= 0.f && tf < t.ms) {
           t.persistent = false;
           t.plane_mask = pm;
@@ -1473,7 +1519,7 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   if (persistent) *persistent = t.persistent ? 1 : 0;
   if (tma_mask)
     *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8) | ((unsigned)(t.plane_cx & 0xF) << 16) |
-                ((t.warp_mask & 0xFFu) << 20);
+                ((t.warp_mask & 0xFFu) << 20) | ((t.prefetch_mask & 0xFu) << 28);
   if (ms) *ms = t.ms;
   if (stage_ms)
     for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
@@ -1489,6 +1535,7 @@ int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigne
   t.plane_mask = (tma_mask >> 8) & 0xFFu;
   t.plane_cx = (int)((tma_mask >> 16) & 0xFu);
   t.warp_mask = (tma_mask >> 20) & 0xFFu;
+  t.prefetch_mask = (tma_mask >> 28) & 0xFu;
   t.ms = 0.f;
   for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;
   return GBFFT_OK;
@@ -1593,6 +1640,13 @@ static const ManyKernel* find_many(const std::vector<int>& codes) {
   }
   return nullptr;
 }
+// Tiles per ticket a length allows: 1, 2, 4 while a team of 256 / S threads
+// still covers threads_for(L) (the 16-pencil tile's natural block size).
+static int many_max_teams(int L) {
+  int s = 1;
+  while (s < 4 && (kManyThreads / (2 * s)) >= threads_for(L)) s *= 2;
+  return s;
+}
 }  // namespace gbfft
 
 struct gbfft_many_s {
@@ -1601,15 +1655,23 @@ struct gbfft_many_s {
   std::vector<gbfft_plan> plans;  // one per grid: twiddles, and the separate-launch path
   std::vector<long long> offs;    // element offset of each grid in the packed buffers
   long long total = 0;            // complex elements of all grids
-  ManySegment* segs[2] = {nullptr, nullptr};  // forward, inverse; stage-major (one launch per stage)
+  // host copy of the segments of each pipeline (forward, inverse), stage-major, teams = 1
+  std::vector<ManySegment> base[2];
+  // tuning: tiles per ticket of each axis length (index L <= 256), per pipeline
+  int teams_by_len[2][257];
+  bool tuned[2] = {false, false};
+  float tuned_ms[2] = {0.f, 0.f};
+  // device tables, rebuilt by many_upload when the tuning changes
+  ManySegment* segs[2] = {nullptr, nullptr};  // stage-major (one launch per stage)
   unsigned int* first[2] = {nullptr, nullptr};
   unsigned char* tile_seg[2] = {nullptr, nullptr};
-  // the one-launch queue's order: stage s of grid g at slot g + s (see gbfft_many_create)
+  // the one-launch queue's order: stage s of grid g at slot g + s (see many_upload)
   ManySegment* segs_q[2] = {nullptr, nullptr};
   unsigned int* first_q[2] = {nullptr, nullptr};
   unsigned char* tile_seg_q[2] = {nullptr, nullptr};
   std::vector<unsigned int> first_host[2];
-  unsigned int tiles[2] = {0, 0};
+  unsigned int tiles[2] = {0, 0};  // tickets of a launch (all stages)
+  unsigned int max_tickets[2] = {0, 0};  // device table capacity (teams = 1)
   int nseg = 0;
   const ManyKernel* kern[2] = {nullptr, nullptr};
   void* ws = nullptr;
@@ -1634,21 +1696,84 @@ static void free_many(gbfft_many_s* m) {
   delete m;
 }
 
+// Build and upload the device tables of pipeline `pipe` for the current
+// tuning: every segment's team count, its tickets (tiles / S, rounded up), the
+// stage-major ticket prefix sums of the per-stage launches and the diagonal
+// queue order of the one-launch schedule: stage s of grid g at slot g + s (z
+// of grid t-2, y of grid t-1, x of grid t share slot t). Every dependency
+// still has a smaller ticket, and only about three grids are in flight at a
+// time, whose intermediates (tens of MB) stay in L2 between their stages.
+// Synchronous (plain copies): not for use during stream capture.
+static int many_upload(gbfft_many_s* m, int pipe) {
+  const int count = m->count;
+  std::vector<ManySegment> segs = m->base[pipe];
+  std::vector<unsigned int> first;
+  std::vector<int> codes;
+  unsigned int acc = 0;
+  for (auto& sg : segs) {
+    const int L = sg.d.L;
+    sg.teams = (L <= 256) ? m->teams_by_len[pipe][L] : 1;
+    if (sg.teams != 1 && sg.teams != 2 && sg.teams != 4) sg.teams = 1;
+    first.push_back(acc);
+    acc += (unsigned int)((sg.d.n_tiles + sg.teams - 1) / sg.teams);
+    const int code = many_code(L, sg.d.dir, sg.teams);
+    if (std::find(codes.begin(), codes.end(), code) == codes.end()) codes.push_back(code);
+  }
+  first.push_back(acc);
+  const ManyKernel* k = find_many(codes);
+  if (!k) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  std::vector<ManySegment> segs_q;
+  std::vector<unsigned int> first_q;
+  unsigned int accq = 0;
+  for (int slot = 0; slot < count + 2; ++slot)
+    for (int st = 2; st >= 0; --st) {
+      const int g = slot - st;
+      if (g < 0 || g >= count) continue;
+      const ManySegment& sg = segs[(size_t)st * count + g];
+      first_q.push_back(accq);
+      accq += (unsigned int)((sg.d.n_tiles + sg.teams - 1) / sg.teams);
+      segs_q.push_back(sg);
+    }
+  first_q.push_back(accq);
+  if (acc > m->max_tickets[pipe] || accq != acc) return GBFFT_ERR_INVALID_ARG;
+  std::vector<unsigned char> ts(acc), tsq(acc);
+  for (size_t sg = 0; sg + 1 < first.size(); ++sg)
+    for (unsigned t = first[sg]; t < first[sg + 1]; ++t) ts[t] = (unsigned char)sg;
+  for (size_t sg = 0; sg + 1 < first_q.size(); ++sg)
+    for (unsigned t = first_q[sg]; t < first_q[sg + 1]; ++t) tsq[t] = (unsigned char)sg;
+  const size_t sb = segs.size() * sizeof(ManySegment), fb = first.size() * sizeof(unsigned int);
+  bool ok = cudaMemcpy(m->segs[pipe], segs.data(), sb, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(m->first[pipe], first.data(), fb, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(m->segs_q[pipe], segs_q.data(), sb, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(m->first_q[pipe], first_q.data(), fb, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok && acc > 0)
+    ok = cudaMemcpy(m->tile_seg[pipe], ts.data(), acc, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(m->tile_seg_q[pipe], tsq.data(), acc, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GBFFT_ERR_CUDA;
+  }
+  m->first_host[pipe] = first;
+  m->tiles[pipe] = acc;
+  m->kern[pipe] = k;
+  return GBFFT_OK;
+}
+
 extern "C" {
 
-int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flags) {
+int gbfft_many_create(gbfft_many* out, int count, const int* dims, int kind, int dtype, unsigned flags) {
   if (!out) return GBFFT_ERR_INVALID_ARG;
   *out = nullptr;
   if (count < 1 || 3 * count > kManyMaxSegs || !dims) return GBFFT_ERR_INVALID_ARG;
+  if (kind != GBFFT_C2C || dtype != GBFFT_FP32) return GBFFT_ERR_INVALID_ARG;  // batching is built for C2C FP32
   if (flags & ~(unsigned)GBFFT_DEBUG_TIMEOUT) return GBFFT_ERR_INVALID_ARG;
   gbfft_many_s* m = new gbfft_many_s();
   m->count = count;
   m->flags = flags;
   cudaGetDevice(&m->device);
-  std::vector<ManySegment> segs[2];
-  std::vector<unsigned int> first[2];
+  for (int pipe = 0; pipe < 2; ++pipe)
+    for (int L = 0; L <= 256; ++L) m->teams_by_len[pipe][L] = 1;
   size_t words = 0;
-  std::vector<int> codes[2];
   for (int g = 0; g < count; ++g) {
     gbfft_plan p = nullptr;
     int rc = gbfft_plan_create(&p, dims[3 * g], dims[3 * g + 1], dims[3 * g + 2], GBFFT_C2C, GBFFT_FP32, 1,
@@ -1680,114 +1805,63 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
       P[g] = build_pipeline(m->plans[g], pipe, op, none, none, none, none);
     }
     const int roles[3][2] = {{0, 1}, {1, 2}, {2, 1}};  // C2C pencil: in->out, out->ws, ws->out
-    std::vector<long long> seg_index(3 * count);
+    std::vector<ManySegment>& segs = m->base[pipe];
     unsigned int acc = 0;
     for (int k = 0; k < 3; ++k)
       for (int g = 0; g < count; ++g) {
-        ManySegment s;
-        std::memset(&s, 0, sizeof(s));
-        s.d = P[g].st[k];
-        s.d.in = nullptr;
-        s.d.out = nullptr;
-        s.in_buf = roles[k][0];
-        s.out_buf = roles[k][1];
-        s.in_off = m->offs[g];
-        s.out_off = m->offs[g];
-        s.c_outer = (long long)words;
-        words += (size_t)s.d.batch * s.d.n_outer;
-        s.c_outer16 = (long long)words;
-        words += (size_t)s.d.batch * gchunks(s.d.n_outer);
-        s.c_gchunk = (long long)words;
-        words += (size_t)s.d.batch * s.d.n_gchunks;
-        s.c_total = (long long)words;
-        words += (size_t)s.d.batch;
-        s.c_stage = (long long)words;
+        ManySegment sg;
+        std::memset(&sg, 0, sizeof(sg));
+        sg.d = P[g].st[k];
+        sg.d.in = nullptr;
+        sg.d.out = nullptr;
+        sg.in_buf = roles[k][0];
+        sg.out_buf = roles[k][1];
+        sg.in_off = m->offs[g];
+        sg.out_off = m->offs[g];
+        sg.teams = 1;
+        sg.c_outer = (long long)words;
+        words += (size_t)sg.d.batch * sg.d.n_outer;
+        sg.c_outer16 = (long long)words;
+        words += (size_t)sg.d.batch * gchunks(sg.d.n_outer);
+        sg.c_gchunk = (long long)words;
+        words += (size_t)sg.d.batch * sg.d.n_gchunks;
+        sg.c_total = (long long)words;
+        words += (size_t)sg.d.batch;
+        sg.c_stage = (long long)words;
         words += 1;
-        s.p_outer = s.p_outer16 = s.p_gchunk = s.p_total = s.p_stage = -1;
-        s.prev_tiles = 0;
+        sg.p_outer = sg.p_outer16 = sg.p_gchunk = sg.p_total = sg.p_stage = -1;
+        sg.prev_tiles = 0;
         if (k > 0) {
-          const ManySegment& q = segs[pipe][(size_t)(k - 1) * count + g];
-          s.p_outer = q.c_outer;
-          s.p_outer16 = q.c_outer16;
-          s.p_gchunk = q.c_gchunk;
-          s.p_total = q.c_total;
-          s.p_stage = q.c_stage;
-          s.prev_tiles = q.d.n_tiles;
+          const ManySegment& q = segs[(size_t)(k - 1) * count + g];
+          sg.p_outer = q.c_outer;
+          sg.p_outer16 = q.c_outer16;
+          sg.p_gchunk = q.c_gchunk;
+          sg.p_total = q.c_total;
+          sg.p_stage = q.c_stage;
+          sg.prev_tiles = q.d.n_tiles;
         }
-        first[pipe].push_back(acc);
-        acc += (unsigned int)s.d.n_tiles;
-        segs[pipe].push_back(s);
-        const int code = kcode(s.d.L, s.d.kind, s.d.dir);
-        if (std::find(codes[pipe].begin(), codes[pipe].end(), code) == codes[pipe].end())
-          codes[pipe].push_back(code);
+        acc += (unsigned int)sg.d.n_tiles;
+        segs.push_back(sg);
       }
     // each segment publishes only the counters its consumer (next stage, same grid) waits on
     for (int k = 0; k + 1 < 3; ++k)
       for (int g = 0; g < count; ++g) {
-        ManySegment& s = segs[pipe][(size_t)k * count + g];
-        const int rule = segs[pipe][(size_t)(k + 1) * count + g].d.dep_rule;
-        s.sig_mask = kSigStage | (rule == kDepGroup ? kSigOuter16 : 0) | (rule == kDepGchunkOfOuter ? kSigGchunk : 0);
+        ManySegment& sg = segs[(size_t)k * count + g];
+        const int rule = segs[(size_t)(k + 1) * count + g].d.dep_rule;
+        sg.sig_mask = kSigStage | (rule == kDepGroup ? kSigOuter16 : 0) | (rule == kDepGchunkOfOuter ? kSigGchunk : 0);
       }
-    first[pipe].push_back(acc);
-    m->first_host[pipe] = first[pipe];
-    m->tiles[pipe] = acc;
-    m->kern[pipe] = find_many(codes[pipe]);
-    if (!m->kern[pipe]) {
-      free_many(m);
-      return GBFFT_ERR_UNSUPPORTED_SIZE;
-    }
+    m->max_tickets[pipe] = acc;
   }
   m->nseg = 3 * count;
   m->counter_words = words;  // forward and inverse counters are laid out side by side
-  // Queue order of the one-launch schedule: stage s of grid g goes to slot g + s (z of grid t-2, y of grid
-  // t-1, x of grid t share slot t). Every dependency still has a smaller ticket, and the grids in flight
-  // at a time are about three, whose intermediates (tens of MB) stay in L2 between their stages, where
-  // the stage-major order of the per-stage launches streams every grid through HBM at every stage.
-  std::vector<ManySegment> segs_q[2];
-  std::vector<unsigned int> first_q[2];
-  for (int pipe = 0; pipe < 2; ++pipe) {
-    unsigned int acc = 0;
-    for (int slot = 0; slot < count + 2; ++slot)
-      for (int k = 2; k >= 0; --k) {
-        const int g = slot - k;
-        if (g < 0 || g >= count) continue;
-        const ManySegment& sg = segs[pipe][(size_t)k * count + g];
-        first_q[pipe].push_back(acc);
-        acc += (unsigned int)sg.d.n_tiles;
-        segs_q[pipe].push_back(sg);
-      }
-    first_q[pipe].push_back(acc);
-  }
   bool ok = true;
   for (int pipe = 0; pipe < 2 && ok; ++pipe) {
-    ok = cudaMalloc(&m->segs_q[pipe], segs_q[pipe].size() * sizeof(ManySegment)) == cudaSuccess &&
-         cudaMemcpy(m->segs_q[pipe], segs_q[pipe].data(), segs_q[pipe].size() * sizeof(ManySegment),
-                    cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMalloc(&m->first_q[pipe], first_q[pipe].size() * sizeof(unsigned int)) == cudaSuccess &&
-         cudaMemcpy(m->first_q[pipe], first_q[pipe].data(), first_q[pipe].size() * sizeof(unsigned int),
-                    cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok) {
-      std::vector<unsigned char> ts(m->tiles[pipe]);
-      for (size_t sg = 0; sg + 1 < first_q[pipe].size(); ++sg)
-        for (unsigned t = first_q[pipe][sg]; t < first_q[pipe][sg + 1]; ++t) ts[t] = (unsigned char)sg;
-      ok = cudaMalloc(&m->tile_seg_q[pipe], std::max<size_t>(ts.size(), 1)) == cudaSuccess &&
-           cudaMemcpy(m->tile_seg_q[pipe], ts.data(), ts.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-    }
-  }
-  for (int pipe = 0; pipe < 2 && ok; ++pipe) {
-    ok = cudaMalloc(&m->segs[pipe], segs[pipe].size() * sizeof(ManySegment)) == cudaSuccess &&
-         cudaMemcpy(m->segs[pipe], segs[pipe].data(), segs[pipe].size() * sizeof(ManySegment),
-                    cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMalloc(&m->first[pipe], first[pipe].size() * sizeof(unsigned int)) == cudaSuccess &&
-         cudaMemcpy(m->first[pipe], first[pipe].data(), first[pipe].size() * sizeof(unsigned int),
-                    cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok) {
-      std::vector<unsigned char> ts(m->tiles[pipe]);
-      for (size_t sg = 0; sg + 1 < first[pipe].size(); ++sg)
-        for (unsigned t = first[pipe][sg]; t < first[pipe][sg + 1]; ++t) ts[t] = (unsigned char)sg;
-      ok = cudaMalloc(&m->tile_seg[pipe], std::max<size_t>(ts.size(), 1)) == cudaSuccess &&
-           cudaMemcpy(m->tile_seg[pipe], ts.data(), ts.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-    }
+    const size_t sb = m->base[pipe].size() * sizeof(ManySegment);
+    const size_t fb = (m->base[pipe].size() + 1) * sizeof(unsigned int);
+    const size_t tb = std::max<size_t>(m->max_tickets[pipe], 1);
+    ok = cudaMalloc(&m->segs[pipe], sb) == cudaSuccess && cudaMalloc(&m->first[pipe], fb) == cudaSuccess &&
+         cudaMalloc(&m->tile_seg[pipe], tb) == cudaSuccess && cudaMalloc(&m->segs_q[pipe], sb) == cudaSuccess &&
+         cudaMalloc(&m->first_q[pipe], fb) == cudaSuccess && cudaMalloc(&m->tile_seg_q[pipe], tb) == cudaSuccess;
   }
   void* c = nullptr;
   ok = ok && cudaMalloc(&m->ws, (size_t)m->total * sizeof(float2)) == cudaSuccess &&
@@ -1801,6 +1875,13 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, unsigned flag
   }
   m->ctl = reinterpret_cast<Control*>(c);
   m->counters = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(c) + sizeof(Control));
+  for (int pipe = 0; pipe < 2; ++pipe) {
+    int rc = many_upload(m, pipe);
+    if (rc) {
+      free_many(m);
+      return rc;
+    }
+  }
   *out = m;
   return GBFFT_OK;
 }
@@ -1844,13 +1925,13 @@ static int many_launch(gbfft_many m, int op, const void* in, void* out, void* st
   if (queue) {
     e = cudaMemsetAsync(&m->ctl->ticket, 0, 2 * sizeof(unsigned int) + m->counter_words * sizeof(unsigned int), st);
     if (e != cudaSuccess) return GBFFT_ERR_CUDA;
-    // one block per ticket (tile); every block a block waits for has started
+    // one block per ticket; every block a block waits for has started
     void* args[] = {&a};
     e = cudaLaunchKernel(k->fn, dim3((unsigned)std::max<unsigned>(a.total, 1u)), dim3(kManyThreads), args, k->smem,
                          st);
     return cuda_err(e);
   }
-  // one launch per stage over every grid's tiles of that stage
+  // one launch per stage over every grid's tickets of that stage
   for (int stg = 0; stg < 3; ++stg) {
     const unsigned lo = m->first_host[pipe][(size_t)stg * m->count];
     const unsigned hi = m->first_host[pipe][(size_t)(stg + 1) * m->count];
@@ -1884,6 +1965,100 @@ int gbfft_many_exec_separate(gbfft_many m, int op, const void* in, void* out, vo
     if (rc) return rc;
   }
   return GBFFT_OK;
+}
+
+// Distinct axis lengths of pipeline `pipe`, largest total tile count first.
+static std::vector<int> many_lengths(const gbfft_many_s* m, int pipe) {
+  std::vector<std::pair<long long, int>> w;
+  for (const auto& sg : m->base[pipe]) {
+    auto it = std::find_if(w.begin(), w.end(), [&](const std::pair<long long, int>& x) { return x.second == sg.d.L; });
+    if (it == w.end()) w.push_back({sg.d.n_tiles, sg.d.L});
+    else it->first += sg.d.n_tiles;
+  }
+  std::sort(w.begin(), w.end(), [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
+    return a.first > b.first;
+  });
+  std::vector<int> out;
+  for (auto& x : w) out.push_back(x.second);
+  return out;
+}
+
+int gbfft_many_autotune(gbfft_many m, void* stream) {
+  if (!m) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void *x = nullptr, *y = nullptr;
+  const size_t bytes = (size_t)std::max<long long>(m->total, 2) * sizeof(float2);
+  if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(x);
+    return GBFFT_ERR_ALLOC;
+  }
+  int rc = cuda_err(cudaMemsetAsync(x, 0, bytes, st));
+  const int reps = 5;
+  for (int pipe = 0; pipe < 2 && !rc; ++pipe) {
+    const int op = pipe == 0 ? GBFFT_OP_FORWARD : GBFFT_OP_INVERSE;
+    auto run = [&] { return many_launch(m, op, x, y, st, true); };
+    for (int L = 0; L <= 256; ++L) m->teams_by_len[pipe][L] = 1;
+    rc = many_upload(m, pipe);
+    if (rc) break;
+    float best = time_calls(run, st, reps);
+    if (best < 0.f) {
+      rc = GBFFT_ERR_CUDA;
+      break;
+    }
+    // coordinate descent over the lengths, two sweeps: each length's tiles per ticket in turn
+    for (int sweep = 0; sweep < 2 && !rc; ++sweep)
+      for (int L : many_lengths(m, pipe)) {
+        const int keep = m->teams_by_len[pipe][L];
+        int best_s = keep;
+        for (int S = 1; S <= many_max_teams(L); S *= 2) {
+          if (S == keep) continue;
+          m->teams_by_len[pipe][L] = S;
+          rc = many_upload(m, pipe);
+          if (rc) break;
+          const float t = time_calls(run, st, reps);
+          if (t >= 0.f && t < best) {
+            best = t;
+            best_s = S;
+          }
+        }
+        if (rc) break;
+        m->teams_by_len[pipe][L] = best_s;
+      }
+    if (!rc) rc = many_upload(m, pipe);
+    m->tuned[pipe] = rc == GBFFT_OK;
+    m->tuned_ms[pipe] = best;
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(x);
+  cudaFree(y);
+  if (!rc && e != cudaSuccess) rc = GBFFT_ERR_CUDA;
+  return rc;
+}
+
+int gbfft_many_get_tuning(gbfft_many m, int pipeline, int* lengths, int* teams, int cap, int* n, float* ms) {
+  if (!m || pipeline < 0 || pipeline > 1 || !n || cap < 0) return GBFFT_ERR_INVALID_ARG;
+  const std::vector<int> ls = many_lengths(m, pipeline);
+  *n = (int)ls.size();
+  for (int i = 0; i < (int)ls.size() && i < cap; ++i) {
+    if (lengths) lengths[i] = ls[i];
+    if (teams) teams[i] = m->teams_by_len[pipeline][ls[i]];
+  }
+  if (ms) *ms = m->tuned[pipeline] ? m->tuned_ms[pipeline] : 0.f;
+  return GBFFT_OK;
+}
+
+int gbfft_many_set_tuning(gbfft_many m, int pipeline, const int* lengths, const int* teams, int n) {
+  if (!m || pipeline < 0 || pipeline > 1 || n < 0 || (n > 0 && (!lengths || !teams))) return GBFFT_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (lengths[i] < 2 || lengths[i] > 256) return GBFFT_ERR_INVALID_ARG;
+    if (teams[i] != 1 && teams[i] != 2 && teams[i] != 4) return GBFFT_ERR_INVALID_ARG;
+    if (teams[i] > many_max_teams(lengths[i])) return GBFFT_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(m->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  for (int i = 0; i < n; ++i) m->teams_by_len[pipeline][lengths[i]] = teams[i];
+  return many_upload(m, pipeline);
 }
 
 int gbfft_many_get_device_error(gbfft_many m, int* code) {

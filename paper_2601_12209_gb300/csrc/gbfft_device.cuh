@@ -301,11 +301,21 @@ struct TileIO {
   float scale;
 };
 
+// Index of the thread within the team of THREADS threads that processes one
+// tile. Every kernel but the batched one runs one team per block (its block
+// size is THREADS, so this is threadIdx.x); the batched kernel runs several
+// tiles of a short length side by side, one per team of consecutive threads.
+template <int THREADS>
+__device__ __forceinline__ int ttid() {
+  static_assert((THREADS & (THREADS - 1)) == 0, "team sizes are powers of two");
+  return (int)(threadIdx.x & (THREADS - 1));
+}
+
 // Row-side load: the transform axis is contiguous in global memory. Lanes run
 // along n (coalesced), each lane moves one pencil pair as a 16-byte smem chunk.
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_load(float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
+  for (int it = ttid<THREADS>(); it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
@@ -319,7 +329,7 @@ template <int THREADS, int NROWS>
 __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
   const float sc = io.scale;
   const bool unit = sc == 1.f;
-  for (int it = threadIdx.x; it < NROWS * 8; it += THREADS) {
+  for (int it = ttid<THREADS>(); it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;
     float4 v = *reinterpret_cast<const float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1)));
@@ -333,7 +343,7 @@ __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
 // along p, so 16 lanes move one 128-byte line.
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
+  for (int it = ttid<THREADS>(); it < NROWS * 16; it += THREADS) {
     int p = it & 15, n = it >> 4;
     float2 a = make_float2(0.f, 0.f);
     if (p < io.valid) a = ld_data(io.gin + p + n * io.in_n);
@@ -343,7 +353,7 @@ __device__ __forceinline__ void col_load(float2* sm, const TileIO& io) {
 
 template <int THREADS, int NROWS>
 __device__ __forceinline__ void col_store(const float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * 16; it += THREADS) {
+  for (int it = ttid<THREADS>(); it < NROWS * 16; it += THREADS) {
     int p = it & 15, n = it >> 4;
     if (p < io.valid) {
       float2 v = sm[swz(n, p)];
@@ -390,7 +400,7 @@ __device__ __forceinline__ void stockham_pass(float2* sm, const float2* tw, cons
   constexpr int G = THREADS / 16;
   constexpr int NBT = (NB + G - 1) / G;
   constexpr int TWO = tw_pass_offset(L, PASS);  // evaluated at compile time
-  const int p = threadIdx.x & 15, g = threadIdx.x >> 4;
+  const int p = ttid<THREADS>() & 15, g = ttid<THREADS>() >> 4;
   float2 v[NBT][R];
   static_for<NBT>([&](auto tc) {
     constexpr int t = decltype(tc)::value;
@@ -1167,11 +1177,14 @@ __device__ __forceinline__ TileIO make_io(const StageDesc& d, long long tile, in
 // Process one tile of one stage. THREADS may exceed threads_for(L) (the
 // persistent kernel runs several lengths with one block size); the extra
 // groups then share the butterflies.
+// idle: the team runs the tile's barriers and arithmetic but reads and writes
+// nothing in global memory (a batched ticket whose last teams have no tile).
 template <int L, int DIR, int KIND, int THREADS, int PREC = kPrecFP32>
 __device__ __forceinline__ void process_tile(const StageDesc& d, long long tile, float2* sm, const float2* tw,
-                                             const float2* tw2) {
+                                             const float2* tw2, bool idle = false) {
   int o, g0;
   TileIO io = make_io(d, tile, o, g0);
+  if (idle) io.valid = 0;
   const bool row_in = d.in_mode == kRow, row_out = d.out_mode == kRow;
   const bool inplace = d.in == d.out;
 

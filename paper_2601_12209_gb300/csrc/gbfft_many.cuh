@@ -13,6 +13,13 @@
 // Segments (one stage of one grid) live in device memory with buffer-relative
 // addresses, so a launch needs only the in / out / workspace base pointers and
 // can be captured in a CUDA graph and replayed.
+//
+// Tile shape (Section III-C's granularity trade-off, chosen per axis length
+// by the batched plan's autotuner): a ticket of a segment carries S = 1, 2 or
+// 4 tiles of 16 pencils, run side by side by S teams of 256 / S threads. At
+// the short lengths one 16-pencil tile keeps only 32-128 threads busy and a
+// block's fixed cost (ticket, descriptor, twiddles, dependency wait, release)
+// is paid per tile; S tiles per ticket fill the block and share that cost.
 #pragma once
 #include "gbfft_kernels.cuh"
 
@@ -24,7 +31,8 @@ struct ManySegment {
   StageDesc d;
   int in_buf, out_buf;  // 0 in, 1 out, 2 workspace
   // counters the consumer segment reads (kSig* bits); the others are not written
-  int sig_mask, sig_pad;
+  int sig_mask;
+  int teams;  // S: tiles per ticket (1, 2 or 4), one team of kManyThreads / S threads each
   long long in_off, out_off;
   // counters of this segment (offsets into the launch's counter buffer)
   long long c_outer, c_outer16, c_gchunk, c_total, c_stage;
@@ -57,19 +65,47 @@ constexpr int kSigOuter16 = 1, kSigGchunk = 2, kSigStage = 4;
 constexpr int kManyThreads = 256;
 constexpr int kManyMaxSegs = 256;  // 3 stages x up to 85 grids per launch
 
+// Kernel code of a batched stage: kcode(L, kPlain, dir) with the team count S in bits 24-26.
+constexpr int many_code(int L, int dir, int S) { return kcode(L, kPlain, dir) | (S << 24); }
+__host__ __device__ constexpr int many_code_len(int c) { return (c >> 8) & 0xFFFF; }
+__host__ __device__ constexpr int many_code_teams(int c) { return c >> 24; }
+
+// Rows of shared tile the kernel needs: S tiles of L + 1 rows (16 pencils each).
 template <int CODE, int... REST>
-__host__ __device__ constexpr int many_max_len() {
-  if constexpr (sizeof...(REST) == 0) return CODE >> 8;
-  else return (CODE >> 8) > many_max_len<REST...>() ? (CODE >> 8) : many_max_len<REST...>();
+__host__ __device__ constexpr int many_max_rows() {
+  constexpr int r = many_code_teams(CODE) * (many_code_len(CODE) + 1);
+  if constexpr (sizeof...(REST) == 0) return r;
+  else return r > many_max_rows<REST...>() ? r : many_max_rows<REST...>();
+}
+
+template <int CODE, int... REST>
+__host__ __device__ constexpr int many_max_tw() {
+  constexpr int t = tw_table_len(many_code_len(CODE));
+  if constexpr (sizeof...(REST) == 0) return t;
+  else return t > many_max_tw<REST...>() ? t : many_max_tw<REST...>();
 }
 
 template <int... CODES>
 constexpr size_t many_smem_bytes() {
-  constexpr int LM = many_max_len<CODES...>();
-  return sizeof(float2) * ((size_t)(LM + 1) * kTileP + (size_t)((max_tw_len<CODES...>() + 7) / 8 * 8));
+  return sizeof(float2) * ((size_t)many_max_rows<CODES...>() * kTileP + (size_t)((many_max_tw<CODES...>() + 7) / 8 * 8));
 }
 
-__device__ __forceinline__ bool many_wait(const ManyArgs& a, const ManySegment& m, long long tile) {
+// Run ticket t0 of a segment with code `code`: team j of the block takes tile t0 * S + j (idle past the end).
+template <int CODE, int... REST>
+__device__ __forceinline__ void many_dispatch(int code, const StageDesc& d, long long t0, float2* sm, const float2* tw) {
+  if (code == CODE) {
+    constexpr int L = many_code_len(CODE), S = many_code_teams(CODE), DIR = (CODE & 1) ? 1 : -1;
+    constexpr int TT = kManyThreads / S;
+    const int team = (int)threadIdx.x / TT;
+    const long long tile = t0 * S + team;
+    const bool idle = tile >= d.n_tiles;
+    process_tile<L, DIR, kPlain, TT>(d, idle ? t0 * S : tile, sm + team * (L + 1) * kTileP, tw, tw, idle);
+  } else if constexpr (sizeof...(REST) > 0) {
+    many_dispatch<REST...>(code, d, t0, sm, tw);
+  }
+}
+
+__device__ __forceinline__ bool many_wait_tile(const ManyArgs& a, const ManySegment& m, long long tile) {
   const StageDesc& d = m.d;
   if (m.p_stage < 0 || d.dep_rule == kDepNone) return true;
   const unsigned int extra = a.debug_never ? 1u : 0u;
@@ -97,7 +133,17 @@ __device__ __forceinline__ bool many_wait(const ManyArgs& a, const ManySegment& 
   }
 }
 
-__device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment& m, long long tile) {
+// Waits for the producer tiles of every tile of ticket t0.
+__device__ __forceinline__ bool many_wait(const ManyArgs& a, const ManySegment& m, long long t0) {
+  for (int j = 0; j < m.teams; ++j) {
+    const long long tile = t0 * m.teams + j;
+    if (tile >= m.d.n_tiles) break;
+    if (!many_wait_tile(a, m, tile)) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void many_signal_tile(const ManyArgs& a, const ManySegment& m, long long tile) {
   const StageDesc& d = m.d;
   // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
   const unsigned t32 = (unsigned)tile;
@@ -107,11 +153,22 @@ __device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment
   const int b = (int)(rest / (unsigned)d.n_outer);
   const int n16 = (d.n_outer + kTileP - 1) / kTileP;
   unsigned int* C = a.counters;
-  if (!m.sig_mask) return;  // last stage of its grid: nobody waits on it
-  __threadfence();
   if (m.sig_mask & kSigOuter16) atomicAdd(C + m.c_outer16 + (long long)b * n16 + o / kTileP, 1u);
   if (m.sig_mask & kSigGchunk) atomicAdd(C + m.c_gchunk + (long long)b * d.n_gchunks + gc, 1u);
-  if (m.sig_mask & kSigStage) atomicAdd(C + m.c_stage, 1u);
+}
+
+// Publishes every tile of ticket t0 (the stage counter once, by the ticket's tile count).
+__device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment& m, long long t0) {
+  if (!m.sig_mask) return;  // last stage of its grid: nobody waits on it
+  __threadfence();
+  unsigned int n = 0;
+  for (int j = 0; j < m.teams; ++j) {
+    const long long tile = t0 * m.teams + j;
+    if (tile >= m.d.n_tiles) break;
+    many_signal_tile(a, m, tile);
+    ++n;
+  }
+  if (m.sig_mask & kSigStage) atomicAdd(a.counters + m.c_stage, n);
 }
 
 // One ticket per block: the block takes the next ticket, finds its segment,
@@ -122,10 +179,9 @@ __device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment
 // registers (inside a tile loop the compiler spills them).
 template <int... CODES>
 __global__ void __launch_bounds__(kManyThreads, 3) many_kernel(ManyArgs a) {
-  constexpr int LM = many_max_len<CODES...>();
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
-  float2* tw = sm + (LM + 1) * kTileP;  // 16-byte aligned: (LM + 1) * 16 float2
+  float2* tw = sm + many_max_rows<CODES...>() * kTileP;  // 16-byte aligned: rows * 16 float2
   __shared__ __align__(16) ManySegment s_seg;
   __shared__ long long s_tile;
   __shared__ unsigned int s_t;
@@ -161,14 +217,14 @@ __global__ void __launch_bounds__(kManyThreads, 3) many_kernel(ManyArgs a) {
   if (!s_ok) return;
   for (int i = threadIdx.x; i < s_seg.d.tw_len; i += kManyThreads) tw[i] = s_seg.d.tw[i];
   __syncthreads();
-  dispatch_tile<kManyThreads, CODES...>(stage_code(s_seg.d), s_seg.d, s_tile, sm, tw, tw);
+  many_dispatch<CODES...>(stage_code(s_seg.d) | (s_seg.teams << 24), s_seg.d, s_tile, sm, tw);
   __syncthreads();
   if (a.queue && threadIdx.x == 0) many_signal(a, s_seg, s_tile);
 }
 
 struct ManyKernel {
   int ncodes;
-  int codes[16];
+  int codes[32];
   const void* fn;
   size_t smem;
 };
@@ -177,6 +233,7 @@ template <int... CODES>
 ManyKernel make_many_entry() {
   ManyKernel k{};
   const int codes[] = {CODES...};
+  static_assert(sizeof...(CODES) <= 32, "ManyKernel holds up to 32 codes");
   k.ncodes = (int)sizeof...(CODES);
   for (int i = 0; i < k.ncodes; ++i) k.codes[i] = codes[i];
   k.fn = reinterpret_cast<const void*>(&many_kernel<CODES...>);

@@ -51,7 +51,7 @@ def test_host_queries(lib):
         assert not abi.gbfft_supported_length(n), n
     with pytest.raises(abi.GbfftError):
         abi.gbfft_radix_plan(7)
-    for code in range(-9, 1):
+    for code in range(-10, 1):
         assert abi.strerror(code) and abi.strerror(code) != "unknown error"
 
 
@@ -69,6 +69,13 @@ def test_invalid_arguments_rejected_before_device(lib):
     assert f(ctypes.byref(h), 7, 8, 8, 0, 0, 1, 0) == abi.GBFFT_ERR_UNSUPPORTED_SIZE
     assert f(ctypes.byref(h), 8, 8, 2048, 0, 0, 1, 0) == abi.GBFFT_ERR_UNSUPPORTED_SIZE
     assert h.value is None
+    dims = (ctypes.c_int * 3)(32, 32, 32)
+    mk = lib.gbfft_many_create
+    assert mk(ctypes.byref(h), 1, dims, abi.GBFFT_R2C, abi.GBFFT_FP32, 0) == abi.GBFFT_ERR_INVALID_ARG  # C2C only
+    assert mk(ctypes.byref(h), 1, dims, abi.GBFFT_C2C, abi.GBFFT_FP16_SPLIT, 0) == abi.GBFFT_ERR_INVALID_ARG
+    assert mk(ctypes.byref(h), 0, dims, abi.GBFFT_C2C, abi.GBFFT_FP32, 0) == abi.GBFFT_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.gbfft_many_autotune(None, None) == abi.GBFFT_ERR_INVALID_ARG
     assert lib.gbfft_exec(None, 0, None, None, None) == abi.GBFFT_ERR_INVALID_ARG
     assert lib.gbfft_workspace_size(None, None) == abi.GBFFT_ERR_INVALID_ARG
     lib.gbfft_plan_destroy(None)

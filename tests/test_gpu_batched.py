@@ -111,3 +111,72 @@ def test_batched_timeout_reported(gb):
     m.exec(abi.GBFFT_OP_FORWARD, x, y)
     assert m.device_error() == abi.GBFFT_ERR_TIMEOUT
     assert m.device_error() == 0
+
+
+def test_batched_tiles_per_ticket_bitwise_and_oracle(gb):
+    """Tiles per ticket (teams of 256 / S threads side by side in one block): every allowed S of
+    every length gives the same bits as one tile per ticket (same butterflies, other threads),
+    in the one launch and the per-stage launches, forward and inverse; ragged last tickets
+    (tile counts not a multiple of S) included; the result matches the FP64 oracle."""
+    from paper_2601_12209_gb300 import abi
+    shapes = [(32, 48, 60), (80, 32, 48), (48, 80, 32), (64, 96, 120), (128, 60, 32), (32, 32, 256),
+              (160, 48, 80), (96, 128, 48)]
+    m = gb.ManyPlan(shapes)
+    grids = [synth.uniform_complex((nz, ny, nx), seed=400 + i) for i, (nx, ny, nz) in enumerate(shapes)]
+    x = m.pack([g.cuda() for g in grids])
+    ref = {}
+    for op in (abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE):
+        y = m.empty()
+        m.exec(op, x, y)
+        ref[op] = y
+    lengths = sorted({v for s in shapes for v in s})
+    maxs = {L: (4 if L in (32, 48, 80) else 2 if L <= 128 else 1) for L in lengths}
+    for S in (2, 4):
+        teams = {L: min(S, maxs[L]) for L in lengths}
+        for pipe in (0, 1):
+            m.set_tuning(pipe, teams)
+        assert m.tuning()["forward"]["teams"] == teams
+        for op in (abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE):
+            y = m.empty()
+            m.exec(op, x, y)
+            y2 = m.empty()
+            m.exec_staged(op, x, y2)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref[op]) and torch.equal(y2, ref[op]), (S, op)
+    assert m.device_error() == 0
+    for i, (g, out) in enumerate(zip(grids, m.unpack(ref[abi.GBFFT_OP_FORWARD]))):
+        assert oracle.rel_l2(out.cpu().numpy(), oracle.fft3(g.numpy())) < TOL
+    with pytest.raises(abi.GbfftError):
+        m.set_tuning(0, {256: 2})  # a length-256 tile already fills the block
+
+
+def test_batched_autotune_config4(gb):
+    """The tile-shape autotuner on the 64 configuration grids: every choice is allowed for its
+    length, the tuned one launch (graph-captured) matches the oracle on sampled grids."""
+    from paper_2601_12209_gb300 import abi
+    shapes, grids = synth.batched_grids(64, seed=6)
+    m = gb.ManyPlan(shapes)
+    tun = m.autotune()
+    print(f"[batched] tuned tiles per ticket: {tun}")
+    for name in ("forward", "inverse"):
+        assert tun[name]["ms"] > 0
+        for L, S in tun[name]["teams"].items():
+            assert S in (1, 2, 4) and (S == 1 or L <= 128)
+    x = m.pack([g.cuda() for g in grids])
+    y = m.empty()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        m.exec(abi.GBFFT_OP_FORWARD, x, y, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        m.exec(abi.GBFFT_OP_FORWARD, x, y)
+    y.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert m.device_error() == 0
+    outs = m.unpack(y)
+    for i in (0, 7, 21, 42, 63):
+        assert oracle.rel_l2(outs[i].cpu().numpy(), oracle.fft3(grids[i].numpy())) < TOL
