@@ -306,8 +306,9 @@ def main():
     ap.add_argument("--ncu-case", default=None,
                     help="run one 512^3 case for a profiler and exit: staged_r2c, staged_lsu_r2c, persistent_r2c, "
                          "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024, "
-                         "split_bf16_1024, split_fp32_1024 (C2C 1024x512x64, staged thread-load launches; "
-                         "tensor-core radix-16 passes unless fp32); or pinned_r2c:<fwd bits>:<inv bits>")
+                         "split_bf16_1024, split_fp16_tc5_1024, split_bf16_tc5_1024, split_fp32_1024 (C2C "
+                         "1024x512x64, staged thread-load launches; tensor-core radix-16 passes unless fp32); "
+                         "or pinned_r2c:<fwd bits>:<inv bits>")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -489,9 +490,13 @@ def ncu_case(name):
     from paper_2601_12209_gb300 import _build, abi
     _build.build()
     if name.startswith("split_"):
-        # split_<fp16|bf16>_1024: C2C 1024 x 512 x 64 (268 MB per buffer), x stage has the tensor-core pass
-        prec = name.split("_")[1]
-        plan = gb.Plan(1024, 512, 64, precision=prec if prec == "fp32" else prec + "_split", staged=True, tma=False)
+        # split_<fp16|bf16|fp32>[_tc5]_1024: C2C 1024 x 512 x 64 (268 MB per buffer), x stage has the tensor-core
+        # pass (warp-level mma.sync, or tcgen05 with _tc5)
+        parts = name.split("_")
+        prec = parts[1]
+        tc5 = "tc5" in parts
+        plan = gb.Plan(1024, 512, 64, precision=prec if prec == "fp32" else prec + "_split" + ("_tc5" if tc5 else ""),
+                       staged=True, tma=False)
         x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
         kind = "c2c"
     elif name.startswith("pinned_r2c"):
@@ -606,7 +611,8 @@ def poisson_variant(torch, gb, abi, stream, steps, warmup):
 
 
 def precision_variant(torch, gb, abi, stream, steps, warmup):
-    """1024^3 C2C: FP32 butterflies vs tensor-core radix-16 passes with FP16 / BF16 hi/lo pairs.
+    """1024^3 C2C: FP32 butterflies vs tensor-core radix-16 passes with FP16 / BF16 hi/lo pairs, as
+    warp-level mma.sync products and as tcgen05.mma products with tensor-memory accumulators.
 
     Timing input: uniform[-1,1] noise drawn on the device from a seeded generator plus 16
     plane waves (the FFT's work does not depend on the values). Accuracy without the oracle:
@@ -627,7 +633,9 @@ def precision_variant(torch, gb, abi, stream, steps, warmup):
     pk = torch.as_tensor(ks, device="cuda")
     out = {"grid": [n, n, n], "flops_5nlog2n": flops_5n(n, n, n), "alg_bytes": c2c_alg_bytes(n, n, n)}
     for name, kw in (("fp32_tuned", {}), ("fp32_staged_lsu", {"staged": True, "tma": False}),
-                     ("fp16_split", {"precision": "fp16_split"}), ("bf16_split", {"precision": "bf16_split"})):
+                     ("fp16_split", {"precision": "fp16_split"}), ("bf16_split", {"precision": "bf16_split"}),
+                     ("fp16_split_tc5", {"precision": "fp16_split_tc5"}),
+                     ("bf16_split_tc5", {"precision": "bf16_split_tc5"})):
         p = gb.Plan(n, n, n, **kw)
         if name == "fp32_tuned":
             p.autotune(stream)

@@ -64,6 +64,15 @@ typedef struct gbfft_plan_s* gbfft_plan;
  * kernel) keep the FP32 butterflies. */
 #define GBFFT_FP16_SPLIT 1
 #define GBFFT_BF16_SPLIT 2
+/* The same split products on the 5th-generation tensor cores: tcgen05.mma
+ * issued by one thread per block, operands in shared memory, FP32
+ * accumulators in tensor memory, 128 butterflies per product (M = 128,
+ * N = 32: the real and imaginary outputs; K = 32: the real and imaginary
+ * inputs). Built for lengths whose radix-16 butterflies fill 128-row tiles
+ * (128, 256, 384, 640, 768, 1024); other lengths with a radix-16 pass take
+ * the warp-level (mma.sync) products of the same operand type. */
+#define GBFFT_FP16_SPLIT_TC5 3
+#define GBFFT_BF16_SPLIT_TC5 4
 
 /* plan flags */
 #define GBFFT_PENCIL 0u          /* three stages, two redistributions (Algorithm 1) */

@@ -51,10 +51,13 @@ class Plan:
     staged: one launch per stage instead of the persistent launch;
     tma=False: staged launches load tiles with thread loads instead of tensor copies;
     precision: "fp32", or "fp16_split" / "bf16_split" (c2c only: radix-16 passes
-    on the tensor cores with hi/lo operand pairs; storage stays complex64).
+    on the tensor cores with hi/lo operand pairs, warp-level mma.sync; storage stays
+    complex64), or "fp16_split_tc5" / "bf16_split_tc5" (the same products as
+    tcgen05.mma on the 5th-generation tensor cores, accumulators in tensor memory).
     """
 
-    _PRECISIONS = {"fp32": abi.GBFFT_FP32, "fp16_split": abi.GBFFT_FP16_SPLIT, "bf16_split": abi.GBFFT_BF16_SPLIT}
+    _PRECISIONS = {"fp32": abi.GBFFT_FP32, "fp16_split": abi.GBFFT_FP16_SPLIT, "bf16_split": abi.GBFFT_BF16_SPLIT,
+                   "fp16_split_tc5": abi.GBFFT_FP16_SPLIT_TC5, "bf16_split_tc5": abi.GBFFT_BF16_SPLIT_TC5}
 
     def __init__(self, nx: int, ny: int, nz: int, kind: str = "c2c", batch: int = 1, slab: bool = False,
                  transposed_out: bool = False, staged: bool = False, debug_timeout: bool = False,

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(PKG, "lib", "libgbfft.so")
 GBFFT_C2C = 0
 GBFFT_R2C = 1
 GBFFT_FP32 = 0
+GBFFT_FP16_SPLIT_TC5 = 3
+GBFFT_BF16_SPLIT_TC5 = 4
 GBFFT_FP16_SPLIT = 1
 GBFFT_BF16_SPLIT = 2
 GBFFT_PENCIL = 0

@@ -34,6 +34,8 @@ void register_split_group_0(std::vector<StageKernel>&);
 void register_split_group_1(std::vector<StageKernel>&);
 void register_split_group_2(std::vector<StageKernel>&);
 void register_split_group_3(std::vector<StageKernel>&);
+void register_tc5_group_0(std::vector<StageKernel>&);
+void register_tc5_group_1(std::vector<StageKernel>&);
 void register_persistent_group_0(std::vector<PersistentKernel>&);
 void register_persistent_group_1(std::vector<PersistentKernel>&);
 void register_tma_group_0(std::vector<TmaKernel>&);
@@ -85,6 +87,8 @@ static void ensure_registry() {
     register_split_group_1(s);
     register_split_group_2(s);
     register_split_group_3(s);
+    register_tc5_group_0(s);
+    register_tc5_group_1(s);
     auto& p = persistent_registry();
     register_persistent_group_0(p);
     register_persistent_group_1(p);
@@ -136,12 +140,19 @@ static bool split_capable(int L) {
 }
 
 // Lengths without tensor-core passes run the same FP32 arithmetic in every
-// precision mode, so a split-precision request takes the FP32 kernel.
+// precision mode, so a split-precision request takes the FP32 kernel; a
+// 5th-generation tensor-core request for a length whose radix-16 butterflies
+// do not fill 128-row operand tiles takes the warp-level (mma.sync) kernel of
+// the same operand type.
 static const StageKernel* find_stage(int L, int dir, int kind, int prec = kPrecFP32) {
   ensure_registry();
   if (prec != kPrecFP32 && !split_capable(L)) prec = kPrecFP32;
-  for (const auto& k : stage_registry())
-    if (k.L == L && k.dir == dir && k.kind == kind && k.prec == prec) return &k;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    for (const auto& k : stage_registry())
+      if (k.L == L && k.dir == dir && k.kind == kind && k.prec == prec) return &k;
+    if (!prec_is_tc5(prec)) break;
+    prec = prec_mma_sync(prec);
+  }
   return nullptr;
 }
 
@@ -557,7 +568,8 @@ static Pipeline build_pipeline(const gbfft_plan_s* p, int pipe, int op, Buf bin,
   }
   for (int s = 0; s < P.n; ++s) {
     StageDesc& d = P.st[s];
-    if (d.kind == kPlain) d.prec = p->dtype;  // GBFFT_*_SPLIT values equal the StagePrec values
+    if (d.kind == kPlain) d.prec = p->dtype;  // GBFFT_*_SPLIT* values equal the StagePrec values
+    d.err = p->ctl ? &p->ctl->error : nullptr;
     d.twn = d.tw == p->tw_x ? p->twn_x : (d.tw == p->tw_y ? p->twn_y : (d.tw == p->tw_z ? p->twn_z : nullptr));
     if (d.kind == kR2CPost || d.kind == kC2RPre) d.twn = p->twn_real;  // length nx = 2 L
   }
@@ -1094,7 +1106,9 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   *out = nullptr;
   if (nx < 2 || ny < 2 || nz < 2 || batch < 1) return GBFFT_ERR_INVALID_ARG;
   if (kind != GBFFT_C2C && kind != GBFFT_R2C) return GBFFT_ERR_INVALID_ARG;
-  if (dtype != GBFFT_FP32 && dtype != GBFFT_FP16_SPLIT && dtype != GBFFT_BF16_SPLIT) return GBFFT_ERR_INVALID_ARG;
+  if (dtype != GBFFT_FP32 && dtype != GBFFT_FP16_SPLIT && dtype != GBFFT_BF16_SPLIT && dtype != GBFFT_FP16_SPLIT_TC5 &&
+      dtype != GBFFT_BF16_SPLIT_TC5)
+    return GBFFT_ERR_INVALID_ARG;
   // split precision: complex transforms only (the real-data and Poisson kinds keep FP32)
   if (dtype != GBFFT_FP32 && kind != GBFFT_C2C) return GBFFT_ERR_INVALID_ARG;
   const unsigned known = GBFFT_SLAB | GBFFT_TRANSPOSED_OUT | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT;

@@ -711,6 +711,311 @@ __device__ __forceinline__ void stockham_pass_tc16(float2* sm, const float2* tw,
   if constexpr (!DST_GLOBAL) __syncthreads();
 }
 
+// ----------------------- split-precision radix 16 on the 5th-generation tensor cores
+//
+// The same split-operand DFT-16 products as stockham_pass_tc16, issued as
+// tcgen05.mma: one thread per block issues them, the operands sit in shared
+// memory and the FP32 accumulators in tensor memory. Butterfly b of the pass
+// (pencil p = b mod 16, group j = b / 16; L butterflies per tile) is row b of
+// an L x 32 operand A = [Re x_0..15 | Im x_0..15] (twiddled inputs scaled by
+// the power of two that puts the row's largest component in [0.5, 1)), split
+// into A_hi and A_lo. The real form of the DFT matrix,
+//   B = [[Fr, Fi], [-Fi, Fr]] (32 x 32, row k = input, column n = output),
+// so that [Yr | Yi] = [Xr | Xi] B, is split into B_hi and B_lo once per block.
+// Each 128-row M-tile m of A gives D_m = A_hi B_lo + A_lo B_hi + A_hi B_hi
+// (small terms first; six MMAs of M = 128, N = 32, K = 16) in tensor-memory
+// columns 32 m .. 32 m + 31, row b in lane b mod 128. A block of THREADS (a
+// multiple of 128) gives thread t the butterflies b = t + THREADS i; warp w may
+// read lanes 32 (w mod 4) .. +31 of tensor memory, which hold b mod 128 =
+// t mod 128, so every thread reads back exactly the rows it packed. While the
+// MMAs run, the tile's data lives in the threads' registers, so A_hi and A_lo
+// (L rows of 64 bytes each) are written over the tile, which holds L + 1 rows
+// of 128 bytes.
+//
+// Operands are K-major with no swizzle: 8-row x 16-byte core matrices, element
+// (row, k) of a 16-bit operand at byte (row / 8) * 512 + (k / 8) * 128 +
+// (row mod 8) * 16 + (k mod 8) * 2 (the descriptor's leading byte offset, 128,
+// steps along K; its stride byte offset, 512, along the rows).
+
+__host__ __device__ constexpr int tc5_ncols(int L) {
+  int need = 32 * (L / 128), c = 32;
+  while (c < need) c *= 2;
+  return c;
+}
+
+// Lengths with a 5th-generation tensor-core pass: a radix-16 pass, butterflies
+// filling 128-row M-tiles, and a block of whole warpgroups.
+__host__ __device__ constexpr bool tc5_capable(int L, int threads) {
+  bool r16 = false;
+  for (int i = 0; i < make_radices(L).n; ++i) r16 = r16 || make_radices(L).r[i] == 16;
+  return r16 && L % 128 == 0 && threads % 128 == 0;
+}
+
+struct Tc5Shared {
+  uint64_t mbar;      // completion of a pass's MMAs (tcgen05.commit)
+  uint32_t tmem;      // tensor-memory base address of the block's accumulators
+  uint32_t phase;     // parity of the next completion
+  int* err;           // plan error word (a bounded wait that ran out records kDevErrTimeout)
+  uint32_t pad;
+  alignas(128) unsigned char b_ops[2][32 * 32 * 2];  // B_hi, B_lo in the operand layout
+};
+
+__device__ __forceinline__ Tc5Shared& tc5_shared() {
+  __shared__ Tc5Shared s;
+  return s;
+}
+
+__device__ __forceinline__ int tc5_off(int row, int k) {
+  return ((row >> 3) << 9) + ((k >> 3) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+__device__ __forceinline__ uint64_t tc5_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t tc5_idesc() {
+  // F32 accumulate, A and B both F16 (0) or both BF16 (1), K-major, N = 32, M = 128
+  constexpr uint32_t f = prec_mma_sync(PREC) == kPrecF16Split ? 0u : 1u;
+  return (1u << 4) | (f << 7) | (f << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// Block prologue: B_hi / B_lo, the completion barrier, tensor memory.
+template <int L, int DIR, int PREC, int THREADS>
+__device__ __forceinline__ void tc5_setup(int* err) {
+  Tc5Shared& c = tc5_shared();
+  const int tid = threadIdx.x;
+  const float sg = DIR < 0 ? -1.f : 1.f;
+  for (int i = tid; i < 32 * 16; i += THREADS) {
+    const int n = i >> 4, k0 = (i & 15) << 1;  // two inputs k0, k0 + 1 of output n
+    float v[2];
+    for (int u = 0; u < 2; ++u) {
+      const int k = k0 + u, q = n & 15, r = k & 15, m = (q * r) & 15;
+      const float cr = cos16(m), si = sg * cos16((m + 12) & 15);  // Fr, Fi of F[q][r]
+      v[u] = n < 16 ? (k < 16 ? cr : -si) : (k < 16 ? si : cr);
+    }
+    uint32_t hi, lo;
+    split16x2<prec_mma_sync(PREC)>(v[0], v[1], hi, lo);
+    *reinterpret_cast<uint32_t*>(c.b_ops[0] + tc5_off(n, k0)) = hi;
+    *reinterpret_cast<uint32_t*>(c.b_ops[1] + tc5_off(n, k0)) = lo;
+  }
+  if (tid == 0) {
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&c.mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    c.phase = 0;
+    c.err = err;
+  }
+  if (tid < 32) {
+    const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&c.tmem);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(tc5_ncols(L))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Block epilogue: every tensor-memory access of the block is done; free it.
+template <int L>
+__device__ __forceinline__ void tc5_teardown() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc5_shared().tmem), "r"(tc5_ncols(L))
+                 : "memory");
+  }
+}
+
+// Bounded wait for the completion of parity `ph` (about 2 s); false if it ran out.
+__device__ __forceinline__ bool tc5_wait(uint32_t mb, uint32_t ph) {
+  uint32_t done = 0;
+  unsigned long long t0 = 0;
+  for (int it = 0; !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(done)
+        : "r"(mb), "r"(ph)
+        : "memory");
+    if (!done && (it & 255) == 255) {
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > 2000000000ull) return false;
+    }
+  }
+  return true;
+}
+
+template <int L, int DIR, int THREADS, int PASS, bool SRC_GLOBAL, bool DST_GLOBAL, int PREC>
+__device__ __forceinline__ void stockham_pass_tc5(float2* sm, const float2* tw, const TileIO& io) {
+  constexpr int R = 16;
+  static_assert(make_radices(L).r[PASS] == R, "tensor-core pass is radix 16");
+  static_assert(tc5_capable(L, THREADS), "128-row M-tiles, whole warpgroups");
+  constexpr int Ns = radix_prefix(L, PASS);
+  constexpr int NB = L / R;
+  constexpr int G = THREADS / 16;
+  constexpr int NBT = (NB + G - 1) / G;
+  constexpr int TWO = tw_pass_offset(L, PASS);
+  constexpr int MT = L / 128;
+  Tc5Shared& c = tc5_shared();
+  const int tid = threadIdx.x;
+  const int p = tid & 15, g = tid >> 4;
+  float2 v[NBT][R];
+  float sc[NBT];
+  // 1. inputs of the thread's butterflies, twiddled, and their power-of-two scale
+  static_for<NBT>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    const int j = g + t * G;
+    sc[t] = 1.f;
+    if (NB % G == 0 || j < NB) {
+      static_for<R>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        const int n = j + r * NB;
+        if constexpr (SRC_GLOBAL) {
+          v[t][r] = (p < io.valid) ? ld_data(io.gin + p + n * io.in_n) : make_float2(0.f, 0.f);
+        } else {
+          v[t][r] = sm[swz(n, p)];
+        }
+      });
+      if constexpr (Ns > 1) {
+        const float2* twp = tw + TWO + (j % Ns) * R;
+        static_for<R / 2>([&](auto hc) {
+          constexpr int r = 2 * decltype(hc)::value;
+          const float4 w = *reinterpret_cast<const float4*>(twp + r);
+          if constexpr (r > 0) v[t][r] = cmul(v[t][r], tw_dir<DIR>(make_float2(w.x, w.y)));
+          v[t][r + 1] = cmul(v[t][r + 1], tw_dir<DIR>(make_float2(w.z, w.w)));
+        });
+      }
+      float m = 0.f;
+      static_for<R>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        m = fmaxf(m, fmaxf(fabsf(v[t][r].x), fabsf(v[t][r].y)));
+      });
+      int e = (int)((__float_as_uint(m) >> 23) & 0xffu);  // m in [2^(e-127), 2^(e-126))
+      e = e == 0 ? 126 : min(e, 252);                      // zero or subnormal row: scale 1
+      sc[t] = __uint_as_float((uint32_t)(e + 1) << 23);    // 2^(e - 126): the output scale
+      const float s_in = __uint_as_float((uint32_t)(253 - e) << 23);  // 2^(126 - e)
+      static_for<R>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        v[t][r] = cscale(v[t][r], s_in);
+      });
+    }
+  });
+  __syncthreads();  // every thread has read the tile: it now takes the operands
+  // 2. rows b of A_hi and A_lo (four 16-byte core-matrix rows each)
+  unsigned char* a_hi = reinterpret_cast<unsigned char*>(sm);
+  unsigned char* a_lo = a_hi + L * 64;
+  static_for<NBT>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    const int j = g + t * G;
+    if (NB % G == 0 || j < NB) {
+      const int b = tid + t * THREADS;
+      static_for<4>([&](auto kc) {
+        constexpr int kg = decltype(kc)::value;  // 0: Re x_0..7, 1: Re x_8..15, 2: Im x_0..7, 3: Im x_8..15
+        uint32_t hi[4], lo[4];
+        static_for<4>([&](auto uc) {
+          constexpr int u = decltype(uc)::value;
+          constexpr int r0 = (kg & 1) * 8 + 2 * u;
+          if constexpr (kg < 2) split16x2<prec_mma_sync(PREC)>(v[t][r0].x, v[t][r0 + 1].x, hi[u], lo[u]);
+          else split16x2<prec_mma_sync(PREC)>(v[t][r0].y, v[t][r0 + 1].y, hi[u], lo[u]);
+        });
+        const int off = tc5_off(b, kg * 8);
+        *reinterpret_cast<uint4*>(a_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      });
+    }
+  });
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&c.mbar);
+  const uint32_t ph = c.phase;
+  // 3. one thread issues the products of every M-tile, then commits them to the barrier
+  if (tid == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t idesc = tc5_idesc<PREC>();
+    const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(a_hi);
+    const uint32_t sa_lo = sa_hi + L * 64;
+    const uint32_t sb_hi = (uint32_t)__cvta_generic_to_shared(c.b_ops[0]);
+    const uint32_t sb_lo = (uint32_t)__cvta_generic_to_shared(c.b_ops[1]);
+    for (int m = 0; m < MT; ++m) {
+      const uint32_t d = c.tmem + 32u * (uint32_t)m;
+      const uint32_t am_hi = sa_hi + (uint32_t)m * 8192u, am_lo = sa_lo + (uint32_t)m * 8192u;
+      const uint32_t as[3] = {am_hi, am_lo, am_hi};
+      const uint32_t bs[3] = {sb_lo, sb_hi, sb_hi};
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t ad = tc5_desc(as[pr] + 256u * ks), bd = tc5_desc(bs[pr] + 256u * ks);
+          const uint32_t acc = (pr | ks) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+  }
+  // 4. wait for the products; every thread reads back its own rows and writes the outputs
+  const bool ok = tc5_wait(mb, ph);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok && c.err) atomicCAS(c.err, 0, kDevErrTimeout);
+  const uint32_t lane_base = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+  static_for<NBT>([&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    const int j = g + t * G;
+    if (NB % G == 0 || j < NB) {
+      const int b = tid + t * THREADS;
+      uint32_t y[32];
+      if (ok) {
+        const uint32_t ta = c.tmem + lane_base + 32u * (uint32_t)(b >> 7);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+            "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]),
+              "=r"(y[8]), "=r"(y[9]), "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15]),
+              "=r"(y[16]), "=r"(y[17]), "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]), "=r"(y[22]),
+              "=r"(y[23]), "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]), "=r"(y[28]), "=r"(y[29]),
+              "=r"(y[30]), "=r"(y[31])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+        for (int u = 0; u < 32; ++u) y[u] = 0u;
+      }
+      const float f = sc[t];
+      if constexpr (DST_GLOBAL) {
+        // last pass (Ns R = L): output q of group j is element j + q NB
+        if (p < io.valid) {
+          float2* o = io.gout + p + (long long)j * io.out_n;
+          const long long step = (long long)NB * io.out_n;
+          const float fs = f * io.scale;
+          static_for<R>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            st_data(o + q * step, make_float2(__uint_as_float(y[q]) * fs, __uint_as_float(y[16 + q]) * fs));
+          });
+        }
+      } else {
+        const int k = j % Ns;
+        const int base = (j - k) * R + k;
+        static_for<R>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          sm[swz(base + q * Ns, p)] = make_float2(__uint_as_float(y[q]) * f, __uint_as_float(y[16 + q]) * f);
+        });
+      }
+    }
+  });
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();  // outputs in the tile; every thread has read the accumulators and the parity
+  if (tid == 0) c.phase = ph ^ 1u;
+}
+
 // All passes of a length-L transform. The data starts in shared memory unless
 // SRC_GLOBAL, and ends in shared memory unless DST_GLOBAL.
 // SRC_LAYOUT selects how pass 0 reads shared memory: 0 the swizzled column
@@ -725,8 +1030,10 @@ __device__ __forceinline__ void fft_passes(float2* sm, const float2* tw, const T
     // before overwriting shared memory, everyone must have read it; a direct
     // global->global single pass in place also needs the barrier
     constexpr bool sync_w = (!src_g && !dst_g) || (src_g && dst_g && INPLACE_GLOBAL);
-    if constexpr (PREC != kPrecFP32 && make_radices(L).r[PASS] == 16 && (PASS > 0 || SRC_LAYOUT == 0)) {
-      stockham_pass_tc16<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, PREC>(sm, tw, io);
+    if constexpr (prec_is_tc5(PREC) && make_radices(L).r[PASS] == 16 && (PASS > 0 || SRC_LAYOUT == 0)) {
+      stockham_pass_tc5<L, DIR, THREADS, PASS, src_g, dst_g, PREC>(sm, tw, io);
+    } else if constexpr (PREC != kPrecFP32 && make_radices(L).r[PASS] == 16 && (PASS > 0 || SRC_LAYOUT == 0)) {
+      stockham_pass_tc16<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, prec_mma_sync(PREC)>(sm, tw, io);
     } else {
       stockham_pass<L, DIR, THREADS, PASS, src_g, dst_g, sync_w, PASS == 0 ? SRC_LAYOUT : 0>(sm, tw, io);
     }

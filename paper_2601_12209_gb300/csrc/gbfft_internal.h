@@ -32,11 +32,22 @@ enum TileKind : int {
 // Arithmetic of a stage's radix-16 passes: FP32 on the CUDA cores, or dense
 // 16x16 DFT products on the tensor cores with operands split into hi/lo pairs
 // of FP16 or BF16 (FP32 accumulation). Storage is complex64 in every mode.
+// The split modes run on the warp-level tensor-core path (mma.sync) or, for
+// lengths whose radix-16 butterflies fill 128-row operand tiles, on the
+// fifth-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
 enum StagePrec : int {
   kPrecFP32 = 0,
   kPrecF16Split = 1,
   kPrecBF16Split = 2,
+  kPrecF16SplitTC5 = 3,
+  kPrecBF16SplitTC5 = 4,
 };
+
+__host__ __device__ constexpr bool prec_is_tc5(int p) { return p == kPrecF16SplitTC5 || p == kPrecBF16SplitTC5; }
+// the warp-level split mode with the same 16-bit operand type
+__host__ __device__ constexpr int prec_mma_sync(int p) {
+  return p == kPrecF16SplitTC5 ? kPrecF16Split : (p == kPrecBF16SplitTC5 ? kPrecBF16Split : p);
+}
 
 // Dependency rule of a tile on the previous stage of the same launch
 // (persistent kernel only). See DepRule handling in the persistent kernel.
@@ -87,6 +98,8 @@ struct StageDesc {
   // row side addresses pencil m at (m / m_split) * split_o + (m % m_split) * split_g.
   int m_split;
   long long split_o, split_g;
+  // device error word of the plan (kernels with bounded waits record kDevErrTimeout here); may be null
+  int* err;
 };
 
 // Control block of one persistent launch (device memory, zeroed before each launch).

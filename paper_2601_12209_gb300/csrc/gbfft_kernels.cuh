@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(stage_threads(L, PREC), stage_min_blocks(L, PR
   float2* tw2 = tw + TWL;
   pdl_launch_next();
   load_twiddles<L, THREADS>(tw, tw2, d, KIND == kR2CPost || KIND == kC2RPre || KIND >= kPoissonZB);
+  if constexpr (prec_is_tc5(PREC)) tc5_setup<L, DIR, PREC, THREADS>(d.err);  // tensor memory, B operands
   __syncthreads();
   pdl_wait_prev();
   if constexpr (stage_loops(L) && KIND == kC2RPre && PREC == kPrecFP32) {
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(stage_threads(L, PREC), stage_min_blocks(L, PR
     if ((long long)blockIdx.x < d.n_tiles)
       process_tile<L, DIR, KIND, THREADS, PREC>(d, (long long)blockIdx.x, sm, tw, tw2);
   }
+  if constexpr (prec_is_tc5(PREC)) tc5_teardown<L>();
 }
 
 template <int L, int DIR, int KIND, int PREC = kPrecFP32>

@@ -1,4 +1,7 @@
-"""Split-precision tensor-core radix-16 passes (C2C): parity with the FP64 oracle.
+"""Split-precision tensor-core radix-16 passes (C2C): parity with the FP64 oracle, for the
+warp-level products (mma.sync, modes *_split) and the 5th-generation ones (tcgen05.mma with
+accumulators in tensor memory, modes *_split_tc5; lengths whose butterflies do not fill 128-row
+operand tiles fall back to the warp-level kernel of the same operand type).
 
 Bounds, from the operand splits (each real operand a = hi + lo, three products
 hi.hi + hi.lo + lo.hi, FP32 accumulation, one power-of-two scale per butterfly):
@@ -18,7 +21,8 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "fp16_split": 1e-5, "bf16_split": 1e-4}
+TOL = {"fp32": 1e-5, "fp16_split": 1e-5, "bf16_split": 1e-4, "fp16_split_tc5": 1e-5, "bf16_split_tc5": 1e-4}
+SPLIT_MODES = ["fp16_split", "bf16_split", "fp16_split_tc5", "bf16_split_tc5"]
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +40,7 @@ def gb():
 SHAPES = [(256, 48, 80), (1024, 24, 60), (128, 240, 48), (80, 768, 16), (640, 40, 48), (384, 96, 32)]
 
 
-@pytest.mark.parametrize("precision", ["fp16_split", "bf16_split"])
+@pytest.mark.parametrize("precision", SPLIT_MODES)
 @pytest.mark.parametrize("shape", SHAPES)
 def test_split_forward_inverse(gb, precision, shape):
     nx, ny, nz = shape
@@ -54,7 +58,7 @@ def test_split_forward_inverse(gb, precision, shape):
     assert e < TOL[precision] and e_inv < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp16_split", "bf16_split"])
+@pytest.mark.parametrize("precision", SPLIT_MODES)
 def test_split_adjoint_and_slab(gb, precision):
     """The adjoint (+ sign, unscaled) and the slab schedule take the same passes."""
     nx, ny, nz = 256, 80, 48
@@ -83,7 +87,7 @@ def test_split_cube_256(gb):
     x = synth.uniform_complex((n, n, n), seed=3)
     ref = oracle.fft3(x.numpy())
     xd = x.cuda()
-    for precision in ("fp32", "fp16_split", "bf16_split"):
+    for precision in ["fp32"] + SPLIT_MODES:
         y = gb.Plan(n, n, n, precision=precision).forward(xd)
         e = oracle.rel_l2(y.cpu().numpy(), ref)
         print(f"[precision] 256^3 {precision}: rel-L2 {e:.3e}")
@@ -120,7 +124,7 @@ def test_precision_1024_plane_waves(gb):
     ky = torch.as_tensor(bins[:, 1], device="cuda")
     kz = torch.as_tensor(bins[:, 2], device="cuda")
     pk = torch.as_tensor(ks, device="cuda")
-    for precision in ("fp32", "fp16_split", "bf16_split"):
+    for precision in ["fp32"] + SPLIT_MODES:
         p = gb.Plan(n, n, n, precision=precision)
         y = p.forward(x)
         got = y[kz, ky, kx].cpu().numpy().astype(np.complex128)
@@ -145,3 +149,25 @@ def test_precision_1024_plane_waves(gb):
         del y, w
         tol = TOL[precision]
         assert e_bins < tol and e_peak < tol and leak < tol and e_rt < tol
+
+
+@pytest.mark.parametrize("precision", ["fp16_split_tc5", "bf16_split_tc5"])
+def test_tc5_staged_transposed_and_batch(gb, precision):
+    """The tcgen05 passes in every stage position: row and column input, pass 0 reading HBM
+    directly, the last pass writing HBM directly (length 256: radix-16 passes 0 and 1),
+    transposed output, two batch entries; bitwise equal on a repeated call (no state carried
+    between calls in tensor memory or the completion barrier)."""
+    nx, ny, nz = 256, 1024, 128
+    x = synth.uniform_complex((2, nz, ny, nx), seed=91)
+    ref = oracle.fft3(x.numpy())
+    p = gb.Plan(nx, ny, nz, batch=2, precision=precision, transposed_out=True)
+    y = p.forward(x.cuda())
+    y2 = p.forward(x.cuda())
+    back = p.inverse(y)
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    assert torch.equal(y, y2)
+    e = oracle.rel_l2(y.cpu().numpy(), np.transpose(ref, (0, 3, 2, 1)))
+    e_rt = oracle.rel_l2(back.cpu().numpy(), x.numpy())
+    print(f"[precision] tc5 {precision} 256x1024x128 batch 2 transposed: fwd {e:.3e}, round trip {e_rt:.3e}")
+    assert e < TOL[precision] and e_rt < TOL[precision]
