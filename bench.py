@@ -679,6 +679,15 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
                                    "tuning": {k: {"persistent": v["persistent"], "tma_mask": v["tma_mask"]}
                                               for k, v in tz.items()}}
     p.close()
+    # the persistent ticket-queue launch with the warp-per-pencil tile body on all three stages
+    p = gb.Plan(N, N, N)
+    for k in (0, 1):
+        abi.gbfft_plan_set_tuning(p.handle, k, True, 0x7 << 20)
+    med, _ = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+    out["c2c_512_persistent_warp_body"] = {
+        "fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
+        "frac": 2 * c2c_alg_bytes(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9 / measured_peaks()[0]}
+    p.close()
     for slab in (False, True):
         p = gb.Plan(N, N, N, slab=slab)
         med, avg = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)

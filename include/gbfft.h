@@ -59,9 +59,11 @@ typedef struct gbfft_plan_s* gbfft_plan;
  * 16x16 DFT products on the tensor cores with each FP32 operand split into a
  * hi/lo pair of FP16 (or BF16) values, three products per term, FP32
  * accumulation, and a power-of-two scale per butterfly. Not in the paper: an
- * extension of its per-axis 1D FFT step (Section III-A). C2C plans only;
- * axes whose length has no radix-16 pass (or is 16 itself, a half-warp
- * kernel) keep the FP32 butterflies. */
+ * extension of its per-axis 1D FFT step (Section III-A). The complex stages
+ * take them (every stage of a C2C plan; the y and z stages of an R2C plan,
+ * whose real x stage and fused Poisson z stage keep FP32); axes whose length
+ * has no radix-16 pass (or is 16 itself, a half-warp kernel) keep the FP32
+ * butterflies. */
 #define GBFFT_FP16_SPLIT 1
 #define GBFFT_BF16_SPLIT 2
 /* The same split products on the 5th-generation tensor cores: tcgen05.mma
@@ -112,8 +114,9 @@ typedef struct gbfft_plan_s* gbfft_plan;
  * Create a plan for `batch` grids of nx x ny x nz (Section V-B: a reusable
  * plan keyed by data type, size, transform type and dimensions).
  *   kind  : GBFFT_C2C or GBFFT_R2C (R2C needs even nx)
- *   dtype : GBFFT_FP32, or GBFFT_FP16_SPLIT / GBFFT_BF16_SPLIT (kind C2C
- *           only; stage launches without tensor copies, whatever the flags)
+ *   dtype : GBFFT_FP32, or GBFFT_FP16_SPLIT / GBFFT_BF16_SPLIT (and their
+ *           _TC5 forms): the complex stages run stage launches without tensor
+ *           copies, whatever the flags
  *   flags : GBFFT_PENCIL or GBFFT_SLAB, optionally | GBFFT_TRANSPOSED_OUT
  *           (pencil only) | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT
  * Every axis length (nx/2 for the R2C x axis) must satisfy
@@ -212,15 +215,16 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
  * and transform type; Section III-C: the granularity/overhead trade-off).
  * For each pipeline of the plan -- 0 forward (FORWARD, INVERSE_ADJOINT),
  * 1 inverse (INVERSE, ADJOINT), 2 Poisson (R2C plans) -- it times on
- * `stream`, with CUDA events, every stage with the thread-load kernel and
- * with the tensor-copy kernel (where one applies), the whole pipeline as
- * one persistent launch (where a kernel family exists) and, for slab plans,
- * each in-plane stage pair as one fused plane launch (a thread-block cluster
- * per xy-plane runs both stages while the plane is in L2); it keeps the
- * fastest. Later exec
- * calls use the choice. Blocking (synchronises `stream`); allocates the
- * plan's workspace and two scratch buffers on first use; respects
- * GBFFT_STAGED and GBFFT_NO_TMA. Do not call it during stream capture.
+ * `stream`, with CUDA events, every stage with each kernel family that
+ * applies (thread loads, tensor copies, warp-per-pencil, the C2R kernel with
+ * cp.async prefetch), the whole pipeline as one persistent launch (where a
+ * kernel family exists; also with the warp-per-pencil tile body on its
+ * length-512 complex stages) and, for slab plans, each in-plane stage pair as
+ * one fused plane launch (a thread-block cluster per xy-plane runs both
+ * stages while the plane is in L2); it keeps the fastest. Later exec calls
+ * use the choice. Blocking (synchronises `stream`); allocates the plan's
+ * workspace and two scratch buffers on first use; respects GBFFT_STAGED and
+ * GBFFT_NO_TMA. Do not call it during stream capture.
  */
 int gbfft_plan_autotune(gbfft_plan plan, void* stream);
 /*
@@ -229,19 +233,25 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
  * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch, bits
  * 16-19 = CTAs per plane cluster of those launches (2, 4, 8; 0 = by plane
  * size), bit 20 + s = stage s runs the warp-per-pencil kernel (lengths 512
- * and 256 complex, and the length-256 real x stages; FP32), *ms = measured time of the choice, stage_ms[0..4] = per-stage times of the
- * staged candidates. Any output pointer may be NULL.
+ * and 256 complex, and the length-256 real x stages; FP32) -- with
+ * *persistent = 1: stage s of the persistent launch runs the warp-per-pencil
+ * tile body (length-512 complex stages of 512-thread families) --, bit
+ * 28 + s (s < 4) = stage s runs the C2R kernel with cp.async prefetch; *ms =
+ * measured time of the choice, stage_ms[0..4] = per-stage times of the staged
+ * candidates. Any output pointer may be NULL.
  */
 int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persistent, unsigned* tma_mask, float* ms,
                           float* stage_ms);
 /*
  * Fix a pipeline's launch choice by hand (as gbfft_plan_autotune would):
- * persistent 1 = one persistent launch (when a kernel family exists), else
- * staged launches with bit s of tma_mask selecting the tensor-copy kernel for
- * stage s (where it applies), bit 8 + s fusing stages s and s+1 into one
- * plane launch (where they are a slab plan's in-plane pair), bits 16-19
- * the CTAs per plane cluster (2, 4 or 8; 0 = by plane size) and bit 20 + s
- * the warp-per-pencil kernel for stage s (where it is built).
+ * persistent 1 = one persistent launch (when a kernel family exists; bit
+ * 20 + s of tma_mask runs stage s on the warp-per-pencil tile body where it
+ * can), else staged launches with bit s of tma_mask selecting the tensor-copy
+ * kernel for stage s (where it applies), bit 8 + s fusing stages s and s+1
+ * into one plane launch (where they are a slab plan's in-plane pair), bits
+ * 16-19 the CTAs per plane cluster (2, 4 or 8; 0 = by plane size), bit 20 + s
+ * the warp-per-pencil kernel for stage s (where it is built) and bit 28 + s
+ * the C2R prefetch kernel for stage s (where it applies).
  */
 int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask);
 /*

@@ -43,6 +43,7 @@ void register_tma_group_1(std::vector<TmaKernel>&);
 void register_tma_group_2(std::vector<TmaKernel>&);
 void register_plane_group_0(std::vector<PlaneKernel>&);
 void register_warp_group_0(std::vector<WarpKernel>&);
+void register_warp_group_1(std::vector<WarpKernel>&);
 void register_prefetch_group_0(std::vector<PrefetchKernel>&);
 
 std::vector<PrefetchKernel>& prefetch_registry() {
@@ -98,6 +99,7 @@ static void ensure_registry() {
     register_tma_group_2(t);
     register_plane_group_0(plane_registry());
     register_warp_group_0(warp_registry());
+    register_warp_group_1(warp_registry());
     register_prefetch_group_0(prefetch_registry());
   });
 }
@@ -815,7 +817,8 @@ static void record_event(gbfft_plan_s* p, cudaStream_t stream, int pipe, bool fi
   ++c.nev;
 }
 
-static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream);
+static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream,
+                          unsigned warp_mask = 0);
 
 // The fused plane kernel for stages s and s+1, if they are the two in-plane
 // stages of a slab pipeline (stage s+1 reads only stage s's tiles of the same
@@ -907,7 +910,7 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
     const PersistentKernel* pk = p->tune[pipe].persistent ? find_persistent(P) : nullptr;
     if (pk) {
       record_event(p, stream, pipe, true);
-      int rc = run_persistent(p, P, pk, stream);
+      int rc = run_persistent(p, P, pk, stream, p->tune[pipe].warp_mask);
       record_event(p, stream, pipe, false);
       return rc;
     }
@@ -927,11 +930,27 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
   return rc;
 }
 
-static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream) {
+// Stages of a persistent launch that can run the warp-per-pencil body (bit s).
+static unsigned persistent_warp_mask(const Pipeline& P, const PersistentKernel* pk) {
+  unsigned m = 0;
+  if (!pk || !pk->warp_body) return 0;
+  for (int s = 0; s < P.n; ++s)
+    if (persistent_warp_body(pk->threads, P.st[s].L, P.st[s].kind) && P.st[s].twn && P.st[s].prec == kPrecFP32)
+      m |= 1u << s;
+  return m;
+}
+
+// warp_mask bit s: stage s runs the warp-per-pencil tile body (where it can).
+static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream,
+                          unsigned warp_mask) {
   PersistentArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nstages = P.n;
-  for (int s = 0; s < P.n; ++s) a.st[s] = P.st[s];
+  const unsigned wm = warp_mask & persistent_warp_mask(P, pk);
+  for (int s = 0; s < P.n; ++s) {
+    a.st[s] = P.st[s];
+    a.st[s].body = (wm >> s) & 1u;
+  }
   long long total = 0;
   for (int s = 0; s < P.n; ++s) total += P.st[s].n_tiles;
   if (total >= (1LL << 31)) return GBFFT_ERR_INVALID_ARG;
@@ -1109,15 +1128,15 @@ int gbfft_plan_create(gbfft_plan* out, int nx, int ny, int nz, int kind, int dty
   if (dtype != GBFFT_FP32 && dtype != GBFFT_FP16_SPLIT && dtype != GBFFT_BF16_SPLIT && dtype != GBFFT_FP16_SPLIT_TC5 &&
       dtype != GBFFT_BF16_SPLIT_TC5)
     return GBFFT_ERR_INVALID_ARG;
-  // split precision: complex transforms only (the real-data and Poisson kinds keep FP32)
-  if (dtype != GBFFT_FP32 && kind != GBFFT_C2C) return GBFFT_ERR_INVALID_ARG;
+  // split precision applies to the complex (kPlain) stages; the real x stage of R2C plans and the
+  // fused Poisson z stages keep FP32
   const unsigned known = GBFFT_SLAB | GBFFT_TRANSPOSED_OUT | GBFFT_STAGED | GBFFT_NO_TMA | GBFFT_DEBUG_TIMEOUT;
   if (flags & ~known) return GBFFT_ERR_INVALID_ARG;
   if ((flags & GBFFT_SLAB) && (flags & GBFFT_TRANSPOSED_OUT)) return GBFFT_ERR_INVALID_ARG;
   if (kind == GBFFT_R2C && (nx % 2 != 0 || nx < 4)) return GBFFT_ERR_INVALID_ARG;
   const int Lx = kind == GBFFT_R2C ? nx / 2 : nx;
   if (!stage_supported(Lx) || !stage_supported(ny) || !stage_supported(nz)) return GBFFT_ERR_UNSUPPORTED_SIZE;
-  for (int L : {nx, ny, nz})
+  for (int L : {kind == GBFFT_R2C ? ny : nx, ny, nz})
     if (dtype != GBFFT_FP32 && (!find_stage(L, -1, kPlain, dtype) || !find_stage(L, 1, kPlain, dtype)))
       return GBFFT_ERR_UNSUPPORTED_SIZE;
   if (kind == GBFFT_R2C && (!find_stage(Lx, -1, kR2CPost) || !find_stage(Lx, 1, kC2RPre)))
@@ -1495,19 +1514,30 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
       staged_ms += best;
     }
     t.ms = staged_ms;
+    // the staged choice; a persistent launch below replaces the masks by its own
+    const unsigned tm = t.tma_mask, wm = t.warp_mask, qm = t.prefetch_mask;
     const PersistentKernel* pk = (plan->flags & GBFFT_STAGED) ? nullptr : find_persistent(P);
     if (pk) {
       float tp = time_calls([&] { return run_persistent(plan, P, pk, st); }, st, reps);
       if (tp >= 0.f && tp < staged_ms) {
         t.persistent = true;
         t.ms = tp;
+        t.tma_mask = t.warp_mask = t.prefetch_mask = 0;
+      }
+      // the same launch with the warp-per-pencil body on its length-512 complex stages
+      const unsigned pw = persistent_warp_mask(P, pk);
+      if (pw) {
+        float tw = time_calls([&] { return run_persistent(plan, P, pk, st, pw); }, st, reps);
+        if (tw >= 0.f && tw < t.ms) {
+          t.persistent = true;
+          t.ms = tw;
+          t.tma_mask = t.prefetch_mask = 0;
+          t.warp_mask = pw;
+        }
       }
     }
     const unsigned pm = (plan->flags & GBFFT_STAGED) ? 0u : plane_mask_of(P);
     if (pm) {
-      const unsigned tm = t.tma_mask;
-      const unsigned wm = t.warp_mask;
-      const unsigned qm = t.prefetch_mask;
       for (int cx : {2, 4, 8}) {
         float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx, wm, qm); }, st, reps);
         if (tf >= 0.f && tf < t.ms) {
@@ -1515,6 +1545,9 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
           t.plane_mask = pm;
           t.plane_cx = cx;
           t.ms = tf;
+          t.tma_mask = tm;
+          t.warp_mask = wm;
+          t.prefetch_mask = qm;
         }
       }
     }

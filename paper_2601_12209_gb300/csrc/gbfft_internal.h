@@ -93,6 +93,7 @@ struct StageDesc {
   int dep_rule;
   int prev_n_outer, prev_n_gchunks;
   int prec;  // StagePrec of the radix-16 passes (kPlain stages of staged launches)
+  int body;  // persistent launches: 1 = this stage's tiles run the warp-per-pencil body (length 512), 0 = Stockham
   // Merged pencil index (warp-per-pencil launches only; 0 = off): the outer
   // and group indices run as one group index m = o * m_split + g, and the
   // row side addresses pencil m at (m / m_split) * split_o + (m % m_split) * split_g.

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "gbfft_device.cuh"
+#include "gbfft_warp_tile.cuh"
 
 namespace gbfft {
 
@@ -24,6 +25,7 @@ struct PersistentKernel {
   int codes[8];  // (L << 8) | (kind << 1) | (dir > 0)
   const void* fn;
   int threads;
+  bool warp_body;  // its length-512 complex stages can run the warp-per-pencil tile body (StageDesc::body)
   size_t smem;               // tile bytes
   size_t tw_smem_per_stage;  // twiddle bytes per stage (total = smem + nstages * this)
 };
@@ -261,11 +263,25 @@ __device__ __forceinline__ void signal_done(const PersistentArgs& a, const Stage
 
 // Runtime dispatch of one tile over the compile-time list of (L, kind, dir)
 // codes this kernel was built for.
+// A length-512 complex stage of a 512-thread persistent block may run the
+// warp-per-pencil body instead (d.body = 1): its twiddle block then holds
+// W_L^(t k1) [k1][t] (L entries) and W_32^(c k2') (32 entries) instead of the
+// packed Stockham table.
+__host__ __device__ constexpr bool persistent_warp_body(int threads, int L, int kind) {
+  return threads == kWarpThreads && L == 512 && kind == kPlain;
+}
+
 template <int THREADS, int CODE, int... REST>
 __device__ __forceinline__ void dispatch_tile(int code, const StageDesc& d, long long tile, float2* sm,
                                               const float2* tw, const float2* tw2) {
   if (code == CODE) {
     constexpr int L = CODE >> 8, KIND = (CODE >> 1) & 127, DIR = (CODE & 1) ? 1 : -1;
+    if constexpr (persistent_warp_body(THREADS, L, KIND)) {
+      if (d.body) {
+        warp_tile<L, DIR, KIND>(d, tile, sm, tw, tw + L, tw2);
+        return;
+      }
+    }
     process_tile<L, DIR, KIND, THREADS>(d, tile, sm, tw, tw2);
   } else if constexpr (sizeof...(REST) > 0) {
     dispatch_tile<THREADS, REST...>(code, d, tile, sm, tw, tw2);
@@ -295,9 +311,21 @@ __host__ __device__ constexpr int family_threads() {
 
 // Shared memory of a persistent launch: the tile, then one twiddle block
 // (W_L, and W_2L for real transforms) per stage of the launch.
+// Tile rows of the warp-per-pencil body (16 padded pencil regions) where a
+// family's block can run it, else 0.
+template <int THREADS, int CODE, int... REST>
+__host__ __device__ constexpr int persistent_warp_rows() {
+  constexpr int L = CODE >> 8;
+  constexpr int r = persistent_warp_body(THREADS, L, (CODE >> 1) & 127) ? kTileP * WarpGeom<512>::kRegion : 0;
+  if constexpr (sizeof...(REST) == 0) return r;
+  else return r > persistent_warp_rows<THREADS, REST...>() ? r : persistent_warp_rows<THREADS, REST...>();
+}
+
 template <int... CODES>
-constexpr size_t persistent_tile_bytes() {
-  return sizeof(float2) * (size_t)(max_len<CODES...>() + 1) * kTileP;
+__host__ __device__ constexpr size_t persistent_tile_bytes() {
+  constexpr int stockham = (max_len<CODES...>() + 1) * kTileP;
+  constexpr int warp = persistent_warp_rows<family_threads<CODES...>(), CODES...>();
+  return sizeof(float2) * (size_t)(stockham > warp ? stockham : warp);
 }
 template <int CODE, int... REST>
 __host__ __device__ constexpr int max_tw_len() {
@@ -325,10 +353,12 @@ template <int... CODES>
 __global__ void __launch_bounds__(family_threads<CODES...>(), min_blocks_for(max_len<CODES...>()))
 persistent_kernel(PersistentArgs a) {
   constexpr int THREADS = family_threads<CODES...>();
-  constexpr int LM = max_len<CODES...>();
   extern __shared__ float4 smem4[];
   float2* sm = reinterpret_cast<float2*>(smem4);
-  float2* tws = sm + (LM + 1) * kTileP;
+  // twiddle blocks after the tile, which is the larger of the Stockham tile and the warp-per-pencil regions
+  constexpr int kTileF2 = (int)(persistent_tile_bytes<CODES...>() / sizeof(float2));
+  static_assert(kTileF2 % 8 == 0, "every stage's twiddle block starts 64-byte aligned");
+  float2* tws = sm + kTileF2;
   __shared__ StageDesc s_st[kMaxStages];
   __shared__ unsigned int s_first[kMaxStages + 1];
   __shared__ int s_complete[kMaxStages];
@@ -349,10 +379,17 @@ persistent_kernel(PersistentArgs a) {
   __syncthreads();
   constexpr int TWB = persistent_tw_block<CODES...>();
   constexpr int TW2 = max_tw_len<CODES...>();
+  static_assert(persistent_warp_rows<THREADS, CODES...>() == 0 || TW2 >= 512 + 32,
+                "the warp-per-pencil tables of a stage fit below its W_2L table");
   for (int s = 0; s < a.nstages; ++s) {
     float2* tw = tws + s * TWB;
     const StageDesc& d = s_st[s];
-    for (int i = threadIdx.x; i < d.tw_len; i += THREADS) tw[i] = d.tw[i];
+    if (d.body) {  // warp-per-pencil tables (length 512: R1 = 16)
+      for (int i = threadIdx.x; i < d.L; i += THREADS) tw[i] = d.twn[(i & 31) * (i >> 5)];
+      if (threadIdx.x < 32) tw[d.L + threadIdx.x] = d.twn[(16 * (threadIdx.x / 16) * (threadIdx.x % 16)) % d.L];
+    } else {
+      for (int i = threadIdx.x; i < d.tw_len; i += THREADS) tw[i] = d.tw[i];
+    }
     if (d.kind == kR2CPost || d.kind == kC2RPre)
       for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[TW2 + i] = d.tw2[i];
   }
@@ -396,6 +433,7 @@ PersistentKernel make_persistent_entry() {
   for (int i = 0; i < k.ncodes; ++i) k.codes[i] = codes[i];
   k.fn = reinterpret_cast<const void*>(&persistent_kernel<CODES...>);
   k.threads = family_threads<CODES...>();
+  k.warp_body = persistent_warp_rows<family_threads<CODES...>(), CODES...>() > 0;
   k.smem = persistent_tile_bytes<CODES...>();
   k.tw_smem_per_stage = persistent_tw_bytes_per_stage<CODES...>();
   return k;

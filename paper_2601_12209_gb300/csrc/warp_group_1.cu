@@ -1,0 +1,13 @@
+// Warp-per-pencil stage kernels of length 1024 (32 values per lane: a radix-32
+// step in registers, one transpose through the warp's region, radix 32 again),
+// forward and inverse.
+#include "gbfft_warp.cuh"
+
+namespace gbfft {
+
+void register_warp_group_1(std::vector<WarpKernel>& v) {
+  v.push_back(make_warp_entry<1024, -1, kPlain>());
+  v.push_back(make_warp_entry<1024, 1, kPlain>());
+}
+
+}  // namespace gbfft

@@ -63,7 +63,7 @@ def test_invalid_arguments_rejected_before_device(lib):
     assert f(ctypes.byref(h), 8, 8, 8, 7, 0, 1, 0) == abi.GBFFT_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 8, 0, 5, 1, 0) == abi.GBFFT_ERR_INVALID_ARG  # no such dtype
     for dt in (abi.GBFFT_FP16_SPLIT, abi.GBFFT_BF16_SPLIT, abi.GBFFT_FP16_SPLIT_TC5, abi.GBFFT_BF16_SPLIT_TC5):
-        assert f(ctypes.byref(h), 8, 8, 8, abi.GBFFT_R2C, dt, 1, 0) == abi.GBFFT_ERR_INVALID_ARG  # split: C2C only
+        assert f(ctypes.byref(h), 9, 8, 8, abi.GBFFT_R2C, dt, 1, 0) == abi.GBFFT_ERR_INVALID_ARG  # odd nx
     assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 0, 0) == abi.GBFFT_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 1, 1 << 20) == abi.GBFFT_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 1, abi.GBFFT_SLAB | abi.GBFFT_TRANSPOSED_OUT) == abi.GBFFT_ERR_INVALID_ARG

@@ -74,9 +74,33 @@ def test_split_adjoint_and_slab(gb, precision):
     assert e_adj < TOL[precision] and e_slab < TOL[precision]
 
 
-def test_split_rejected_for_real_transforms(gb):
-    with pytest.raises(Exception):
-        gb.Plan(64, 64, 64, kind="r2c", precision="fp16_split")
+@pytest.mark.parametrize("precision", SPLIT_MODES)
+@pytest.mark.parametrize("shape", [(64, 256, 48), (40, 80, 768), (256, 1024, 16)], ids=lambda s: "x".join(map(str, s)))
+def test_split_r2c_c2r_and_poisson(gb, precision, shape):
+    """R2C plans in the split modes: the complex y and z stages take the tensor-core radix-16 passes
+    (the real x stage and the fused Poisson z stage keep FP32); forward, inverse, adjoint and the
+    Poisson solve against the FP64 oracle."""
+    nx, ny, nz = shape
+    r = synth.normal_real((nz, ny, nx), seed=50 + ny)
+    p = gb.Plan(nx, ny, nz, kind="r2c", precision=precision)
+    s = p.forward(r.cuda())
+    back = p.inverse(s)
+    adj = p.adjoint(s)
+    phi = p.poisson(r.cuda())
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    sh = s.cpu().numpy().astype("complex128")
+    e = oracle.rel_l2(s.cpu().numpy(), oracle.rfft3(r.numpy()))
+    e_rt = oracle.rel_l2(back.cpu().numpy(), r.numpy())
+    e_adj = oracle.rel_l2(adj.cpu().numpy(), oracle.r2c_adjoint(sh, nx))
+    e_p = oracle.rel_l2(phi.cpu().numpy(), oracle.poisson(r.numpy()))
+    print(f"[precision] r2c {precision} {shape}: fwd {e:.3e}, round trip {e_rt:.3e}, adjoint {e_adj:.3e}, "
+          f"poisson {e_p:.3e}")
+    tol = TOL[precision]
+    assert e < tol and e_rt < tol and e_adj < tol and e_p < tol
+
+
+def test_split_rejected_for_unknown_precision(gb):
     with pytest.raises(ValueError):
         gb.Plan(64, 64, 64, precision="fp8")
 

@@ -109,3 +109,54 @@ def test_warp_merged_z_pencils(gb, shape, slab, batch):
     print(f"[warp] merged z {shape} slab={slab} batch={batch}: fwd {e:.3e}, round trip {e_rt:.3e}, "
           f"adjoint {e_adj:.3e}")
     assert e < TOL and e_rt < TOL and e_adj < TOL
+
+
+def test_persistent_launch_with_warp_body_c2c_512_cube(gb):
+    """The persistent ticket-queue launch (one launch per transform, bounded per-chunk dependency
+    waits) running the warp-per-pencil tile body on its length-512 stages: the same bits as the
+    staged warp-per-pencil launches, and the FP64 oracle, forward and inverse at 512^3 C2C."""
+    from paper_2601_12209_gb300 import abi
+    n = 512
+    x = synth.uniform_complex((n, n, n), seed=3)
+    xd = x.cuda()
+    p = gb.Plan(n, n, n)
+    for pipe in (0, 1):
+        abi.gbfft_plan_set_tuning(p.handle, pipe, True, 0x7 << 20)
+    t = abi.gbfft_plan_get_tuning(p.handle, 0)
+    assert t["persistent"] and (t["tma_mask"] >> 20) & 0x7 == 0x7
+    y = p.forward(xd)
+    z = p.inverse(y)
+    s = gb.Plan(n, n, n, staged=True)
+    _pin_warp(s)
+    ys = s.forward(xd)
+    zs = s.inverse(ys)
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    assert torch.equal(y, ys) and torch.equal(z, zs)
+    e = oracle.rel_l2(y.cpu().numpy(), oracle.fft3(x.numpy()))
+    e_rt = oracle.rel_l2(z.cpu().numpy(), x.numpy())
+    print(f"[warp] persistent warp body c2c 512^3: fwd {e:.3e}, round trip {e_rt:.3e}")
+    assert e < TOL and e_rt < TOL
+
+
+@pytest.mark.parametrize("shape,slab,batch", [((1024, 24, 20), False, 1), ((24, 1024, 20), False, 2),
+                                              ((20, 24, 1024), False, 1), ((1024, 1024, 2), True, 1),
+                                              ((48, 1024, 40), False, 1)])
+def test_warp1024_c2c(gb, shape, slab, batch):
+    """Length-1024 warp-per-pencil stages (32 values per lane, radix 32 in registers twice): every
+    stage position (row and column input and output, in place in the slab schedule, merged z
+    pencils), forward, inverse and adjoint against the FP64 oracle."""
+    nx, ny, nz = shape
+    x = synth.uniform_complex((batch, nz, ny, nx), seed=95 + nx + ny)
+    p = gb.Plan(nx, ny, nz, batch=batch, slab=slab)
+    _pin_warp(p)
+    y = p.forward(x.cuda())
+    z = p.inverse(y)
+    a = p.adjoint(x.cuda())
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
+    e = oracle.rel_l2(y.cpu().numpy(), oracle.fft3(x.numpy()))
+    e_rt = oracle.rel_l2(z.cpu().numpy(), x.numpy())
+    e_adj = oracle.rel_l2(a.cpu().numpy(), oracle.c2c_adjoint(x.numpy()))
+    print(f"[warp] 1024 {shape} slab={slab} batch={batch}: fwd {e:.3e}, round trip {e_rt:.3e}, adjoint {e_adj:.3e}")
+    assert e < TOL and e_rt < TOL and e_adj < TOL
