@@ -308,7 +308,9 @@ def main():
                          "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024, "
                          "split_bf16_1024, split_fp16_tc5_1024, split_bf16_tc5_1024, split_fp32_1024 (C2C "
                          "1024x512x64, staged thread-load launches; tensor-core radix-16 passes unless fp32); "
-                         "or pinned_r2c:<fwd bits>:<inv bits>")
+                         "or pinned_r2c:<fwd bits>:<inv bits>, persistent_warp_c2c (C2C 512^3, one persistent "
+                         "launch with warp-per-pencil tile bodies), warp1024_c2c (C2C 1024x512x64, warp-per-pencil "
+                         "stages)")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args.ncu_case)
@@ -499,6 +501,20 @@ def ncu_case(name):
                        staged=True, tma=False)
         x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
         kind = "c2c"
+    elif name == "persistent_warp_c2c":
+        # C2C 512^3 as one persistent launch per transform, warp-per-pencil tile body on all three stages
+        kind = "c2c"
+        plan = gb.Plan(N, N, N)
+        for k in (0, 1):
+            abi.gbfft_plan_set_tuning(plan.handle, k, True, 0x7 << 20)
+        x = synth.uniform_complex((N, N, N), seed=3).cuda()
+    elif name == "warp1024_c2c":
+        # C2C 1024 x 512 x 64 (268 MB per buffer): the x stage on the length-1024 warp-per-pencil kernel
+        kind = "c2c"
+        plan = gb.Plan(1024, 512, 64, staged=True)
+        for k in (0, 1):
+            abi.gbfft_plan_set_tuning(plan.handle, k, False, 0xFF << 20)
+        x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
     elif name.startswith("pinned_r2c"):
         # pinned_r2c:<forward bits>:<inverse bits>: R2C 512^3 with a fixed launch choice (the tuning bits of
         # gbfft_plan_set_tuning), e.g. the benchmark's autotuned choice, so a profile sees the timed kernels

@@ -973,6 +973,7 @@ static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKe
   const bool dbg = (p->flags & GBFFT_DEBUG_TIMEOUT) != 0;
   a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
   a.debug_never = dbg ? 1 : 0;
+  for (int s = 0; s < P.n; ++s) a.sig[s] = s + 1 < P.n ? persistent_sig_for_rule(P.st[s + 1].dep_rule) : 0;
   cudaError_t e = cudaMemsetAsync(&p->ctl->ticket, 0, 2 * sizeof(unsigned int) + p->counters_words * sizeof(unsigned int),
                                   stream);
   if (e != cudaSuccess) return GBFFT_ERR_CUDA;

@@ -170,7 +170,19 @@ struct PersistentArgs {
   unsigned int* cnt_stage[kMaxStages];   // one per stage
   long long timeout_ns;                  // bound on every dependency wait
   int debug_never;                       // wait for one more completion than exists (timeout test)
+  // counters a stage's tiles publish: the one the next stage's rule waits on
+  // and the stage total (kPSig* bits); 0 for the last stage (nobody waits)
+  int sig[kMaxStages];
 };
+
+constexpr int kPSigOuter = 1, kPSigOuter16 = 2, kPSigGchunk = 4, kPSigTotal = 8, kPSigStage = 16;
+
+// The counters stage s + 1 reads under its dependency rule (plus the stage total,
+// which every wait checks first).
+__host__ __device__ constexpr int persistent_sig_for_rule(int rule) {
+  return kPSigStage | (rule == kDepGroup ? kPSigOuter16 : 0) | (rule == kDepOuter ? kPSigOuter : 0) |
+         (rule == kDepGchunkOfOuter || rule == kDepSameGchunk ? kPSigGchunk : 0) | (rule == kDepAll ? kPSigTotal : 0);
+}
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
@@ -253,12 +265,16 @@ __device__ __forceinline__ void signal_done(const PersistentArgs& a, const Stage
   const int o = (int)(rest % (unsigned)d.n_outer);
   const int b = (int)(rest / (unsigned)d.n_outer);
   const int n16 = (d.n_outer + kTileP - 1) / kTileP;
-  __threadfence();
-  atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);
-  atomicAdd(a.cnt_outer16[s] + (long long)b * n16 + o / kTileP, 1u);
-  atomicAdd(a.cnt_gchunk[s] + (long long)b * d.n_gchunks + gc, 1u);
-  atomicAdd(a.cnt_total[s] + b, 1u);
-  atomicAdd(a.cnt_stage[s], 1u);
+  const int sig = a.sig[s];
+  if (!sig) return;  // last stage of the launch: nobody waits on it
+  // release fence: the block's stores (observed through the barrier) before the
+  // counter updates, which consumers read with ld.acquire
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  if (sig & kPSigOuter) atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);
+  if (sig & kPSigOuter16) atomicAdd(a.cnt_outer16[s] + (long long)b * n16 + o / kTileP, 1u);
+  if (sig & kPSigGchunk) atomicAdd(a.cnt_gchunk[s] + (long long)b * d.n_gchunks + gc, 1u);
+  if (sig & kPSigTotal) atomicAdd(a.cnt_total[s] + b, 1u);
+  if (sig & kPSigStage) atomicAdd(a.cnt_stage[s], 1u);
 }
 
 // Runtime dispatch of one tile over the compile-time list of (L, kind, dir)

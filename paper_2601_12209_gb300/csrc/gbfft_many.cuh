@@ -160,7 +160,8 @@ __device__ __forceinline__ void many_signal_tile(const ManyArgs& a, const ManySe
 // Publishes every tile of ticket t0 (the stage counter once, by the ticket's tile count).
 __device__ __forceinline__ void many_signal(const ManyArgs& a, const ManySegment& m, long long t0) {
   if (!m.sig_mask) return;  // last stage of its grid: nobody waits on it
-  __threadfence();
+  // release fence: the block's stores (observed through the barrier) before the counter updates
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
   unsigned int n = 0;
   for (int j = 0; j < m.teams; ++j) {
     const long long tile = t0 * m.teams + j;
