@@ -210,6 +210,46 @@ __device__ __forceinline__ bool wait_counter(const unsigned int* p, unsigned int
   return true;
 }
 
+// The counter tile `tile` of stage s waits on under its stage's rule, and the
+// count it waits for (*target); nullptr when it waits for nothing (first
+// stage, no rule, or the producer stage already known complete).
+__device__ __forceinline__ const unsigned int* dep_counter(const PersistentArgs& a, const StageDesc* st,
+                                                          const int* complete, int s, long long tile,
+                                                          unsigned int* target) {
+  if (s == 0) return nullptr;
+  const StageDesc& d = st[s];
+  if (d.dep_rule == kDepNone || complete[s - 1]) return nullptr;
+  const unsigned int extra = a.debug_never ? 1u : 0u;
+  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
+  const unsigned t32 = (unsigned)tile;
+  const unsigned gc = t32 % (unsigned)d.n_gchunks;
+  const unsigned rest = t32 / (unsigned)d.n_gchunks;
+  const int o = (int)(rest % (unsigned)d.n_outer);
+  const int b = (int)(rest / (unsigned)d.n_outer);
+  switch (d.dep_rule) {
+    case kDepGroup: {
+      // the consumer's group chunk gc is the producer's outer chunk gc
+      const int n16 = (d.prev_n_outer + kTileP - 1) / kTileP;
+      const int outers = min(kTileP, d.prev_n_outer - (int)gc * kTileP);
+      *target = (unsigned int)(outers * d.prev_n_gchunks) + extra;
+      return a.cnt_outer16[s - 1] + (long long)b * n16 + gc;
+    }
+    case kDepOuter:
+      *target = (unsigned int)d.prev_n_gchunks + extra;
+      return a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + o;
+    case kDepGchunkOfOuter:
+      *target = (unsigned int)d.prev_n_outer + extra;
+      return a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + o / kTileP;
+    case kDepSameGchunk:
+      *target = (unsigned int)d.prev_n_outer + extra;
+      return a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + gc;
+    case kDepAll:
+      *target = (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra;
+      return a.cnt_total[s - 1] + b;
+  }
+  return nullptr;
+}
+
 // Wait for the producer tiles (previous stage) that tile `tile` of stage s reads.
 // One counter per rule; `complete` caches "the whole previous stage is done".
 __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDesc* st, int* complete, int s,
@@ -222,35 +262,9 @@ __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDe
     complete[s - 1] = 1;
     return true;
   }
-  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
-  const unsigned t32 = (unsigned)tile;
-  const unsigned gc = t32 % (unsigned)d.n_gchunks;
-  const unsigned rest = t32 / (unsigned)d.n_gchunks;
-  const int o = (int)(rest % (unsigned)d.n_outer);
-  const int b = (int)(rest / (unsigned)d.n_outer);
-  const unsigned long long t0 = global_ns();
-  switch (d.dep_rule) {
-    case kDepGroup: {
-      // the consumer's group chunk gc is the producer's outer chunk gc
-      const int n16 = (d.prev_n_outer + kTileP - 1) / kTileP;
-      const int outers = min(kTileP, d.prev_n_outer - (int)gc * kTileP);
-      return wait_counter(a.cnt_outer16[s - 1] + (long long)b * n16 + gc,
-                          (unsigned int)(outers * d.prev_n_gchunks) + extra, a.ctl, a.timeout_ns, t0);
-    }
-    case kDepOuter:
-      return wait_counter(a.cnt_outer[s - 1] + (long long)b * d.prev_n_outer + o,
-                          (unsigned int)d.prev_n_gchunks + extra, a.ctl, a.timeout_ns, t0);
-    case kDepGchunkOfOuter:
-      return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + o / kTileP,
-                          (unsigned int)d.prev_n_outer + extra, a.ctl, a.timeout_ns, t0);
-    case kDepSameGchunk:
-      return wait_counter(a.cnt_gchunk[s - 1] + (long long)b * d.prev_n_gchunks + gc,
-                          (unsigned int)d.prev_n_outer + extra, a.ctl, a.timeout_ns, t0);
-    case kDepAll:
-      return wait_counter(a.cnt_total[s - 1] + b, (unsigned int)(d.prev_n_outer * d.prev_n_gchunks) + extra, a.ctl,
-                          a.timeout_ns, t0);
-  }
-  return true;
+  unsigned int target = 0;
+  const unsigned int* p = dep_counter(a, st, complete, s, tile, &target);
+  return p ? wait_counter(p, target, a.ctl, a.timeout_ns, global_ns()) : true;
 }
 
 // Publish a finished tile. Called by one thread after a block barrier: the
@@ -410,34 +424,69 @@ persistent_kernel(PersistentArgs a) {
       for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[TW2 + i] = d.tw2[i];
   }
   __syncthreads();
-  unsigned int next = 0;
-  for (;;) {
-    const unsigned int t = s_ticket;
+  // Worker loop with a look-ahead of one tile. Thread 0 holds the ticket after
+  // the current one (t1) and fetches the one after that (t2) while the block
+  // works; at the start of a tile it also issues the acquire load of the
+  // counter t1 waits on. When the tile ends the block then usually knows that
+  // t1's producers are complete and starts t1 without a block barrier, while
+  // thread 0 publishes the finished tile; otherwise thread 0 publishes it and
+  // then waits (bounded) for t1's producers before the block goes on. Every
+  // tile is published before its block waits for anything, so every wait is
+  // for tiles of blocks that are running. Slot (iteration & 1) of s_tk / s_go
+  // is written by thread 0 one iteration ahead of its readers.
+  __shared__ unsigned int s_tk[2];
+  __shared__ int s_go[2];
+  unsigned int t1 = 0, t2 = 0;
+  if (threadIdx.x == 0) {
+    s_tk[0] = s_ticket;
+    s_go[0] = 0;
+    t1 = atomicAdd(&a.ctl->ticket, 1u);
+  }
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int slot = it & 1;
+    const unsigned int t = s_tk[slot];
     if (t >= a.total) break;
     int s = 0;
     while (s + 1 < a.nstages && t >= s_first[s + 1]) ++s;
     const long long tile = (long long)(t - s_first[s]);
-    if (threadIdx.x == 0) {
-      next = atomicAdd(&a.ctl->ticket, 1u);  // prefetch: the result is needed after the tile
-      int ok = *reinterpret_cast<volatile int*>(&a.ctl->abort) ? 0 : 1;
-      if (ok && !wait_deps(a, s_st, s_complete, s, tile)) {
-        atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
-        atomicExch(&a.ctl->abort, 1);
-        ok = 0;
+    if (!s_go[slot]) {
+      if (threadIdx.x == 0) {
+        int ok = *reinterpret_cast<volatile int*>(&a.ctl->abort) ? 0 : 1;
+        if (ok && !wait_deps(a, s_st, s_complete, s, tile)) {
+          atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
+          atomicExch(&a.ctl->abort, 1);
+          ok = 0;
+        }
+        s_ok = ok;
       }
-      s_ok = ok;
+      __syncthreads();
+      if (!s_ok) break;
     }
-    __syncthreads();
-    if (!s_ok) break;
+    // look ahead: the next ticket's producer counter, loaded while this tile runs
+    const unsigned int* lp = nullptr;
+    unsigned int lv = 0, ltarget = 0;
+    if (threadIdx.x == 0) {
+      t2 = atomicAdd(&a.ctl->ticket, 1u);  // needed one tile later
+      if (t1 < a.total) {
+        int s1 = 0;
+        while (s1 + 1 < a.nstages && t1 >= s_first[s1 + 1]) ++s1;
+        lp = dep_counter(a, s_st, s_complete, s1, (long long)(t1 - s_first[s1]), &ltarget);
+        if (lp) lv = ld_acquire(lp);
+      }
+    }
     const StageDesc& d = s_st[s];
     const float2* tw = tws + s * TWB;
     dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile, sm, tw, tw + TW2);
+    if (threadIdx.x == 0) {
+      s_tk[slot ^ 1] = t1;
+      s_go[slot ^ 1] = (t1 >= a.total || !lp || lv >= ltarget) ? 1 : 0;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       signal_done(a, s_st, s, tile);
-      s_ticket = next;
+      t1 = t2;
     }
-    __syncthreads();
   }
 }
 
