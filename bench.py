@@ -576,7 +576,8 @@ def batched_variant(torch, gb, abi, stream, steps, warmup):
     g1 = graph_of(one)
     res["one_launch_graph_one_tile_per_ticket"] = timed(lambda: g1.replay())
     del g1
-    res["tuning"] = {k: {"tiles_per_ticket": v["teams"], "ms": v["ms"]} for k, v in m.autotune(stream).items()}
+    res["tuning"] = {k: {"tiles_per_ticket": v["teams"], "queue_lag": v["lag"], "ms": v["ms"]}
+                     for k, v in m.autotune(stream).items()}
     graph = graph_of(one)
     graph3 = graph_of(lambda: m.exec_staged(abi.GBFFT_OP_FORWARD, x, y, stream=stream))
     for name, fn in (("one_launch_graph", lambda: graph.replay()),

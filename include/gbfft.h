@@ -369,6 +369,11 @@ int gbfft_many_autotune(gbfft_many m, void* stream);
 int gbfft_many_get_tuning(gbfft_many m, int pipeline, int* lengths, int* teams, int cap, int* n, float* ms);
 /* Set tiles per ticket by hand (teams 1, 2 or 4, at most what the length allows; synchronous upload). */
 int gbfft_many_set_tuning(gbfft_many m, int pipeline, const int* lengths, const int* teams, int n);
+/* Queue lag of the one launch (chosen by gbfft_many_autotune from 1, 2, 4): stage s of grid g is queued at
+   slot g + s * lag, so a larger lag queues a grid's next stage further behind its producer. Every dependency
+   keeps a smaller ticket for any lag. set: 1..8 (synchronous upload; not during stream capture). */
+int gbfft_many_get_lag(gbfft_many m, int pipeline, int* lag);
+int gbfft_many_set_lag(gbfft_many m, int pipeline, int lag);
 /* Read and clear the device error word of the batched launches (synchronises). */
 int gbfft_many_get_device_error(gbfft_many m, int* code);
 void gbfft_many_destroy(gbfft_many m);

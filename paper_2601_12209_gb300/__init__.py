@@ -263,7 +263,14 @@ class ManyPlan:
         return self.tuning()
 
     def tuning(self) -> dict:
-        return {name: abi.gbfft_many_get_tuning(self.handle, k) for k, name in enumerate(("forward", "inverse"))}
+        out = {}
+        for k, name in enumerate(("forward", "inverse")):
+            out[name] = abi.gbfft_many_get_tuning(self.handle, k)
+            out[name]["lag"] = abi.gbfft_many_get_lag(self.handle, k)
+        return out
+
+    def set_lag(self, pipeline: int, lag: int) -> None:
+        abi.gbfft_many_set_lag(self.handle, pipeline, lag)
 
     def set_tuning(self, pipeline: int, teams: dict) -> None:
         abi.gbfft_many_set_tuning(self.handle, pipeline, teams)

@@ -59,7 +59,8 @@ EXPORTED = (
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
     "gbfft_plan_set_tuning", "gbfft_many_create", "gbfft_many_layout", "gbfft_many_exec",
     "gbfft_many_exec_separate", "gbfft_many_get_device_error", "gbfft_many_destroy", "gbfft_many_exec_staged",
-    "gbfft_many_autotune", "gbfft_many_get_tuning", "gbfft_many_set_tuning",
+    "gbfft_many_autotune", "gbfft_many_get_tuning", "gbfft_many_set_tuning", "gbfft_many_get_lag",
+    "gbfft_many_set_lag",
 )
 
 _lib = None
@@ -118,6 +119,8 @@ def load() -> ctypes.CDLL:
             "gbfft_many_get_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), i, ctypes.POINTER(i),
                                           ctypes.POINTER(ctypes.c_float)]),
             "gbfft_many_set_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), i]),
+            "gbfft_many_get_lag": (i, [vp, i, ctypes.POINTER(i)]),
+            "gbfft_many_set_lag": (i, [vp, i, i]),
             "gbfft_many_layout": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
             "gbfft_many_exec": (i, [vp, i, vp, vp, vp]),
             "gbfft_many_exec_separate": (i, [vp, i, vp, vp, vp]),
@@ -311,6 +314,16 @@ def gbfft_many_get_tuning(m: int, pipeline: int) -> dict:
     _call("gbfft_many_get_tuning", ctypes.c_void_p(m), int(pipeline), lens, teams, cap, ctypes.byref(n),
           ctypes.byref(ms))
     return {"teams": {int(lens[i]): int(teams[i]) for i in range(min(n.value, cap))}, "ms": ms.value}
+
+
+def gbfft_many_get_lag(m: int, pipeline: int) -> int:
+    v = ctypes.c_int()
+    _call("gbfft_many_get_lag", ctypes.c_void_p(m), int(pipeline), ctypes.byref(v))
+    return v.value
+
+
+def gbfft_many_set_lag(m: int, pipeline: int, lag: int) -> None:
+    _call("gbfft_many_set_lag", ctypes.c_void_p(m), int(pipeline), int(lag))
 
 
 def gbfft_many_set_tuning(m: int, pipeline: int, teams: dict) -> None:

@@ -1707,6 +1707,8 @@ struct gbfft_many_s {
   std::vector<ManySegment> base[2];
   // tuning: tiles per ticket of each axis length (index L <= 256), per pipeline
   int teams_by_len[2][257];
+  // queue lag of the one launch: stage s of grid g takes slot g + s * lag
+  int lag[2] = {1, 1};
   bool tuned[2] = {false, false};
   float tuned_ms[2] = {0.f, 0.f};
   // device tables, rebuilt by many_upload when the tuning changes
@@ -1747,10 +1749,11 @@ static void free_many(gbfft_many_s* m) {
 // Build and upload the device tables of pipeline `pipe` for the current
 // tuning: every segment's team count, its tickets (tiles / S, rounded up), the
 // stage-major ticket prefix sums of the per-stage launches and the diagonal
-// queue order of the one-launch schedule: stage s of grid g at slot g + s (z
-// of grid t-2, y of grid t-1, x of grid t share slot t). Every dependency
-// still has a smaller ticket, and only about three grids are in flight at a
-// time, whose intermediates (tens of MB) stay in L2 between their stages.
+// queue order of the one-launch schedule: stage s of grid g at slot
+// g + s * lag (lag 1: z of grid t-2, y of grid t-1, x of grid t share slot
+// t). Every dependency still has a smaller ticket, and only a few grids are
+// in flight at a time, whose intermediates (tens of MB) stay in L2 between
+// their stages; a longer lag queues a consumer further behind its producer.
 // Synchronous (plain copies): not for use during stream capture.
 static int many_upload(gbfft_many_s* m, int pipe) {
   const int count = m->count;
@@ -1773,9 +1776,10 @@ static int many_upload(gbfft_many_s* m, int pipe) {
   std::vector<ManySegment> segs_q;
   std::vector<unsigned int> first_q;
   unsigned int accq = 0;
-  for (int slot = 0; slot < count + 2; ++slot)
+  const int lag = m->lag[pipe];
+  for (int slot = 0; slot < count + 2 * lag; ++slot)
     for (int st = 2; st >= 0; --st) {
-      const int g = slot - st;
+      const int g = slot - st * lag;
       if (g < 0 || g >= count) continue;
       const ManySegment& sg = segs[(size_t)st * count + g];
       first_q.push_back(accq);
@@ -2048,6 +2052,7 @@ int gbfft_many_autotune(gbfft_many m, void* stream) {
     const int op = pipe == 0 ? GBFFT_OP_FORWARD : GBFFT_OP_INVERSE;
     auto run = [&] { return many_launch(m, op, x, y, st, true); };
     for (int L = 0; L <= 256; ++L) m->teams_by_len[pipe][L] = 1;
+    m->lag[pipe] = 1;
     rc = many_upload(m, pipe);
     if (rc) break;
     float best = time_calls(run, st, reps);
@@ -2074,6 +2079,17 @@ int gbfft_many_autotune(gbfft_many m, void* stream) {
         if (rc) break;
         m->teams_by_len[pipe][L] = best_s;
       }
+    // queue lag between a grid's stages
+    for (int lag : {2, 4}) {
+      if (rc) break;
+      const int keep = m->lag[pipe];
+      m->lag[pipe] = lag;
+      rc = many_upload(m, pipe);
+      if (rc) break;
+      const float t = time_calls(run, st, reps);
+      if (t >= 0.f && t < best) best = t;
+      else m->lag[pipe] = keep;
+    }
     if (!rc) rc = many_upload(m, pipe);
     m->tuned[pipe] = rc == GBFFT_OK;
     m->tuned_ms[pipe] = best;
@@ -2095,6 +2111,19 @@ int gbfft_many_get_tuning(gbfft_many m, int pipeline, int* lengths, int* teams, 
   }
   if (ms) *ms = m->tuned[pipeline] ? m->tuned_ms[pipeline] : 0.f;
   return GBFFT_OK;
+}
+
+int gbfft_many_get_lag(gbfft_many m, int pipeline, int* lag) {
+  if (!m || pipeline < 0 || pipeline > 1 || !lag) return GBFFT_ERR_INVALID_ARG;
+  *lag = m->lag[pipeline];
+  return GBFFT_OK;
+}
+
+int gbfft_many_set_lag(gbfft_many m, int pipeline, int lag) {
+  if (!m || pipeline < 0 || pipeline > 1 || lag < 1 || lag > 8) return GBFFT_ERR_INVALID_ARG;
+  if (cudaSetDevice(m->device) != cudaSuccess) return GBFFT_ERR_CUDA;
+  m->lag[pipeline] = lag;
+  return many_upload(m, pipeline);
 }
 
 int gbfft_many_set_tuning(gbfft_many m, int pipeline, const int* lengths, const int* teams, int n) {

@@ -148,6 +148,17 @@ def test_batched_tiles_per_ticket_bitwise_and_oracle(gb):
         assert oracle.rel_l2(out.cpu().numpy(), oracle.fft3(g.numpy())) < TOL
     with pytest.raises(abi.GbfftError):
         m.set_tuning(0, {256: 2})  # a length-256 tile already fills the block
+    # the queue lag between a grid's stages reorders tickets only: same bits
+    for lag in (2, 4, 8):
+        for pipe in (0, 1):
+            m.set_lag(pipe, lag)
+        assert m.tuning()["inverse"]["lag"] == lag
+        for op in (abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE):
+            y = m.empty()
+            m.exec(op, x, y)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref[op]), (lag, op)
+    assert m.device_error() == 0
 
 
 def test_batched_autotune_config4(gb):
@@ -159,7 +170,7 @@ def test_batched_autotune_config4(gb):
     tun = m.autotune()
     print(f"[batched] tuned tiles per ticket: {tun}")
     for name in ("forward", "inverse"):
-        assert tun[name]["ms"] > 0
+        assert tun[name]["ms"] > 0 and tun[name]["lag"] in (1, 2, 4)
         for L, S in tun[name]["teams"].items():
             assert S in (1, 2, 4) and (S == 1 or L <= 128)
     x = m.pack([g.cuda() for g in grids])
