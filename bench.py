@@ -513,7 +513,7 @@ def ncu_case(name):
         kind = "c2c"
         plan = gb.Plan(1024, 512, 64, staged=True)
         for k in (0, 1):
-            abi.gbfft_plan_set_tuning(plan.handle, k, False, 0xFF << 20)
+            abi.gbfft_plan_set_tuning(plan.handle, k, False, 0x1F << 20)
         x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
     elif name.startswith("pinned_r2c"):
         # pinned_r2c:<forward bits>:<inverse bits>: R2C 512^3 with a fixed launch choice (the tuning bits of
@@ -696,15 +696,19 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
                                    "tuning": {k: {"persistent": v["persistent"], "tma_mask": v["tma_mask"]}
                                               for k, v in tz.items()}}
     p.close()
-    # the persistent ticket-queue launch with the warp-per-pencil tile body on all three stages
-    p = gb.Plan(N, N, N)
-    for k in (0, 1):
-        abi.gbfft_plan_set_tuning(p.handle, k, True, 0x7 << 20)
-    med, _ = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
-    out["c2c_512_persistent_warp_body"] = {
-        "fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
-        "frac": 2 * c2c_alg_bytes(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9 / measured_peaks()[0]}
-    p.close()
+    # the persistent ticket-queue launch with the warp-per-pencil tile body on all three stages, with 1, 2 and 4
+    # consecutive tiles per ticket
+    pw = {}
+    for log_t in (0, 1, 2):
+        p = gb.Plan(N, N, N)
+        for k in (0, 1):
+            abi.gbfft_plan_set_tuning(p.handle, k, True, (0x7 << 20) | (log_t << 25))
+        med, _ = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+        pw[f"tiles_per_ticket_{1 << log_t}"] = {
+            "fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
+            "frac": 2 * c2c_alg_bytes(N, N, N) / ((med[0] + med[1]) * 1e-3) / 1e9 / measured_peaks()[0]}
+        p.close()
+    out["c2c_512_persistent_warp_body"] = pw
     for slab in (False, True):
         p = gb.Plan(N, N, N, slab=slab)
         med, avg = time_variant(torch, p, x, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)

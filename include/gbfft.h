@@ -218,8 +218,8 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
  * `stream`, with CUDA events, every stage with each kernel family that
  * applies (thread loads, tensor copies, warp-per-pencil, the C2R kernel with
  * cp.async prefetch), the whole pipeline as one persistent launch (where a
- * kernel family exists; also with the warp-per-pencil tile body on its
- * length-512 complex stages) and, for slab plans, each in-plane stage pair as
+ * kernel family exists; with 1, 2 or 4 consecutive tiles per ticket, and also
+ * with the warp-per-pencil tile body on its length-512 complex stages) and, for slab plans, each in-plane stage pair as
  * one fused plane launch (a thread-block cluster per xy-plane runs both
  * stages while the plane is in L2); it keeps the fastest. Later exec calls
  * use the choice. Blocking (synchronises `stream`); allocates the plan's
@@ -232,10 +232,11 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
  * *persistent 0/1, *tma_mask bit s (0-7) = stage s uses the tensor-copy
  * kernel, bit 8 + s = stages s and s+1 run as one fused plane launch, bits
  * 16-19 = CTAs per plane cluster of those launches (2, 4, 8; 0 = by plane
- * size), bit 20 + s = stage s runs the warp-per-pencil kernel (lengths 512
+ * size), bit 20 + s (s < 5) = stage s runs the warp-per-pencil kernel (lengths 1024, 512
  * and 256 complex, and the length-256 real x stages; FP32) -- with
  * *persistent = 1: stage s of the persistent launch runs the warp-per-pencil
- * tile body (length-512 complex stages of 512-thread families) --, bit
+ * tile body (length-512 complex stages of 512-thread families) --, bits
+ * 25-26 = log2 of the persistent launch's tiles per ticket (1, 2, 4), bit
  * 28 + s (s < 4) = stage s runs the C2R kernel with cp.async prefetch; *ms =
  * measured time of the choice, stage_ms[0..4] = per-stage times of the staged
  * candidates. Any output pointer may be NULL.
@@ -246,7 +247,8 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
  * Fix a pipeline's launch choice by hand (as gbfft_plan_autotune would):
  * persistent 1 = one persistent launch (when a kernel family exists; bit
  * 20 + s of tma_mask runs stage s on the warp-per-pencil tile body where it
- * can), else staged launches with bit s of tma_mask selecting the tensor-copy
+ * can, bits 25-26 give log2 of its tiles per ticket, 3 is invalid), else
+ * staged launches with bit s of tma_mask selecting the tensor-copy
  * kernel for stage s (where it applies), bit 8 + s fusing stages s and s+1
  * into one plane launch (where they are a slab plan's in-plane pair), bits
  * 16-19 the CTAs per plane cluster (2, 4 or 8; 0 = by plane size), bit 20 + s

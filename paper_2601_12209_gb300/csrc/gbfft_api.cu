@@ -306,6 +306,7 @@ struct gbfft_plan_s {
     unsigned plane_mask = 0;  // bit s: stages s and s+1 run as one fused plane launch
     unsigned warp_mask = 0;   // bit s: stage s runs the warp-per-pencil kernel
     unsigned prefetch_mask = 0;  // bit s: stage s runs the cp.async prefetch C2R kernel
+    int persistent_tiles = 1;    // persistent launch: consecutive tiles per ticket (1, 2, 4)
     int plane_cx = 0;         // CTAs per plane cluster of the fused launches (0: by plane size)
     float ms = 0.f;         // measured time of the chosen launch(es)
     float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -818,7 +819,7 @@ static void record_event(gbfft_plan_s* p, cudaStream_t stream, int pipe, bool fi
 }
 
 static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream,
-                          unsigned warp_mask = 0);
+                          unsigned warp_mask = 0, int tiles_per_ticket = 1);
 
 // The fused plane kernel for stages s and s+1, if they are the two in-plane
 // stages of a slab pipeline (stage s+1 reads only stage s's tiles of the same
@@ -910,7 +911,7 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
     const PersistentKernel* pk = p->tune[pipe].persistent ? find_persistent(P) : nullptr;
     if (pk) {
       record_event(p, stream, pipe, true);
-      int rc = run_persistent(p, P, pk, stream, p->tune[pipe].warp_mask);
+      int rc = run_persistent(p, P, pk, stream, p->tune[pipe].warp_mask, p->tune[pipe].persistent_tiles);
       record_event(p, stream, pipe, false);
       return rc;
     }
@@ -942,17 +943,19 @@ static unsigned persistent_warp_mask(const Pipeline& P, const PersistentKernel* 
 
 // warp_mask bit s: stage s runs the warp-per-pencil tile body (where it can).
 static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream,
-                          unsigned warp_mask) {
+                          unsigned warp_mask, int tiles_per_ticket) {
   PersistentArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nstages = P.n;
+  if (tiles_per_ticket != 1 && tiles_per_ticket != 2 && tiles_per_ticket != 4) return GBFFT_ERR_INVALID_ARG;
+  a.tiles_per_ticket = tiles_per_ticket;
   const unsigned wm = warp_mask & persistent_warp_mask(P, pk);
   for (int s = 0; s < P.n; ++s) {
     a.st[s] = P.st[s];
     a.st[s].body = (wm >> s) & 1u;
   }
   long long total = 0;
-  for (int s = 0; s < P.n; ++s) total += P.st[s].n_tiles;
+  for (int s = 0; s < P.n; ++s) total += (P.st[s].n_tiles + tiles_per_ticket - 1) / tiles_per_ticket;
   if (total >= (1LL << 31)) return GBFFT_ERR_INVALID_ARG;
   a.total = (unsigned int)total;
   a.ctl = p->ctl;
@@ -1519,22 +1522,21 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
     const unsigned tm = t.tma_mask, wm = t.warp_mask, qm = t.prefetch_mask;
     const PersistentKernel* pk = (plan->flags & GBFFT_STAGED) ? nullptr : find_persistent(P);
     if (pk) {
-      float tp = time_calls([&] { return run_persistent(plan, P, pk, st); }, st, reps);
-      if (tp >= 0.f && tp < staged_ms) {
-        t.persistent = true;
-        t.ms = tp;
-        t.tma_mask = t.warp_mask = t.prefetch_mask = 0;
-      }
-      // the same launch with the warp-per-pencil body on its length-512 complex stages
+      // one launch per transform: Stockham tile bodies, then the warp-per-pencil body on its length-512
+      // complex stages, each with 1, 2 or 4 tiles per ticket
       const unsigned pw = persistent_warp_mask(P, pk);
-      if (pw) {
-        float tw = time_calls([&] { return run_persistent(plan, P, pk, st, pw); }, st, reps);
-        if (tw >= 0.f && tw < t.ms) {
-          t.persistent = true;
-          t.ms = tw;
-          t.tma_mask = t.prefetch_mask = 0;
-          t.warp_mask = pw;
+      for (unsigned wmask : {0u, pw}) {
+        for (int tpt : {1, 2, 4}) {
+          float tp = time_calls([&] { return run_persistent(plan, P, pk, st, wmask, tpt); }, st, reps);
+          if (tp >= 0.f && tp < t.ms) {
+            t.persistent = true;
+            t.ms = tp;
+            t.tma_mask = t.prefetch_mask = 0;
+            t.warp_mask = wmask;
+            t.persistent_tiles = tpt;
+          }
         }
+        if (pw == 0u) break;
       }
     }
     const unsigned pm = (plan->flags & GBFFT_STAGED) ? 0u : plane_mask_of(P);
@@ -1567,7 +1569,8 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   if (persistent) *persistent = t.persistent ? 1 : 0;
   if (tma_mask)
     *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8) | ((unsigned)(t.plane_cx & 0xF) << 16) |
-                ((t.warp_mask & 0xFFu) << 20) | ((t.prefetch_mask & 0xFu) << 28);
+                ((t.warp_mask & 0x1Fu) << 20) | ((unsigned)(t.persistent_tiles == 4 ? 2 : t.persistent_tiles == 2 ? 1 : 0) << 25) |
+                ((t.prefetch_mask & 0xFu) << 28);
   if (ms) *ms = t.ms;
   if (stage_ms)
     for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
@@ -1576,13 +1579,15 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
 
 int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask) {
   if (!plan || pipeline < 0 || pipeline > 2) return GBFFT_ERR_INVALID_ARG;
+  if (((tma_mask >> 25) & 0x3u) == 3u) return GBFFT_ERR_INVALID_ARG;  // tiles per ticket 1, 2 or 4
   gbfft_plan_s::Tuning& t = plan->tune[pipeline];
   t.tuned = true;
   t.persistent = persistent != 0;
   t.tma_mask = tma_mask & 0xFFu;
   t.plane_mask = (tma_mask >> 8) & 0xFFu;
   t.plane_cx = (int)((tma_mask >> 16) & 0xFu);
-  t.warp_mask = (tma_mask >> 20) & 0xFFu;
+  t.warp_mask = (tma_mask >> 20) & 0x1Fu;
+  t.persistent_tiles = 1 << ((tma_mask >> 25) & 0x3u);
   t.prefetch_mask = (tma_mask >> 28) & 0xFu;
   t.ms = 0.f;
   for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;

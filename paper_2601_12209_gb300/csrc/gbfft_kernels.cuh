@@ -173,7 +173,12 @@ struct PersistentArgs {
   // counters a stage's tiles publish: the one the next stage's rule waits on
   // and the stage total (kPSig* bits); 0 for the last stage (nobody waits)
   int sig[kMaxStages];
+  // consecutive tiles of one stage per ticket (1, 2 or 4): the ticket, the
+  // dependency look-ahead and the publishing fence are paid once per ticket
+  int tiles_per_ticket;
 };
+
+constexpr int kMaxTicketTiles = 4;
 
 constexpr int kPSigOuter = 1, kPSigOuter16 = 2, kPSigGchunk = 4, kPSigTotal = 8, kPSigStage = 16;
 
@@ -187,6 +192,12 @@ __host__ __device__ constexpr int persistent_sig_for_rule(int rule) {
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -267,28 +278,31 @@ __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDe
   return p ? wait_counter(p, target, a.ctl, a.timeout_ns, global_ns()) : true;
 }
 
-// Publish a finished tile. Called by one thread after a block barrier: the
+// Publish ntiles finished tiles from tile0 on. Called by one thread after a block barrier: the
 // fence orders the whole block's stores (observed through the barrier) before
 // the counter updates that consumers acquire.
-__device__ __forceinline__ void signal_done(const PersistentArgs& a, const StageDesc* st, int s, long long tile) {
+__device__ __forceinline__ void signal_done(const PersistentArgs& a, const StageDesc* st, int s, long long tile0,
+                                            int ntiles) {
   const StageDesc& d = st[s];
-  // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
-  const unsigned t32 = (unsigned)tile;
-  const unsigned gc = t32 % (unsigned)d.n_gchunks;
-  const unsigned rest = t32 / (unsigned)d.n_gchunks;
-  const int o = (int)(rest % (unsigned)d.n_outer);
-  const int b = (int)(rest / (unsigned)d.n_outer);
-  const int n16 = (d.n_outer + kTileP - 1) / kTileP;
   const int sig = a.sig[s];
   if (!sig) return;  // last stage of the launch: nobody waits on it
   // release fence: the block's stores (observed through the barrier) before the
   // counter updates, which consumers read with ld.acquire
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
-  if (sig & kPSigOuter) atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);
-  if (sig & kPSigOuter16) atomicAdd(a.cnt_outer16[s] + (long long)b * n16 + o / kTileP, 1u);
-  if (sig & kPSigGchunk) atomicAdd(a.cnt_gchunk[s] + (long long)b * d.n_gchunks + gc, 1u);
-  if (sig & kPSigTotal) atomicAdd(a.cnt_total[s] + b, 1u);
-  if (sig & kPSigStage) atomicAdd(a.cnt_stage[s], 1u);
+  const int n16 = (d.n_outer + kTileP - 1) / kTileP;
+  for (int j = 0; j < ntiles; ++j) {
+    // 32-bit decode (tile counts stay below 2^32): 64-bit division is a subroutine call
+    const unsigned t32 = (unsigned)(tile0 + j);
+    const unsigned gc = t32 % (unsigned)d.n_gchunks;
+    const unsigned rest = t32 / (unsigned)d.n_gchunks;
+    const int o = (int)(rest % (unsigned)d.n_outer);
+    const int b = (int)(rest / (unsigned)d.n_outer);
+    if (sig & kPSigOuter) atomicAdd(a.cnt_outer[s] + (long long)b * d.n_outer + o, 1u);
+    if (sig & kPSigOuter16) atomicAdd(a.cnt_outer16[s] + (long long)b * n16 + o / kTileP, 1u);
+    if (sig & kPSigGchunk) atomicAdd(a.cnt_gchunk[s] + (long long)b * d.n_gchunks + gc, 1u);
+    if (sig & kPSigTotal) atomicAdd(a.cnt_total[s] + b, 1u);
+  }
+  if (sig & kPSigStage) atomicAdd(a.cnt_stage[s], (unsigned int)ntiles);
 }
 
 // Runtime dispatch of one tile over the compile-time list of (L, kind, dir)
@@ -401,7 +415,7 @@ persistent_kernel(PersistentArgs a) {
       s_st[k] = a.st[k];
       s_first[k] = acc;
       s_complete[k] = 0;
-      if (k < a.nstages) acc += (unsigned int)a.st[k].n_tiles;
+      if (k < a.nstages) acc += (unsigned int)((a.st[k].n_tiles + a.tiles_per_ticket - 1) / a.tiles_per_ticket);
     }
     s_first[kMaxStages] = acc;
     s_ticket = atomicAdd(&a.ctl->ticket, 1u);
@@ -424,16 +438,18 @@ persistent_kernel(PersistentArgs a) {
       for (int i = threadIdx.x; i <= d.L; i += THREADS) tw[TW2 + i] = d.tw2[i];
   }
   __syncthreads();
-  // Worker loop with a look-ahead of one tile. Thread 0 holds the ticket after
-  // the current one (t1) and fetches the one after that (t2) while the block
-  // works; at the start of a tile it also issues the acquire load of the
-  // counter t1 waits on. When the tile ends the block then usually knows that
-  // t1's producers are complete and starts t1 without a block barrier, while
-  // thread 0 publishes the finished tile; otherwise thread 0 publishes it and
-  // then waits (bounded) for t1's producers before the block goes on. Every
-  // tile is published before its block waits for anything, so every wait is
-  // for tiles of blocks that are running. Slot (iteration & 1) of s_tk / s_go
-  // is written by thread 0 one iteration ahead of its readers.
+  // Worker loop with a look-ahead of one ticket. A ticket is T consecutive
+  // tiles of one stage (T = a.tiles_per_ticket). Thread 0 holds the ticket
+  // after the current one (t1) and fetches the one after that (t2) while the
+  // block works; at the start of a ticket it also reads the counters t1's
+  // tiles wait on (relaxed loads, then an acquire fence). When they are already
+  // complete the block starts t1 after this ticket without a block barrier,
+  // while thread 0 publishes the finished tiles; otherwise thread 0 publishes
+  // them and then waits (bounded) for t1's producers before the block goes on. Every tile is published before its block waits for
+  // anything, so every wait is for tiles of blocks that are running. Slot
+  // (iteration & 1) of s_tk / s_go is written by thread 0 one iteration ahead
+  // of its readers.
+  const int T = a.tiles_per_ticket;
   __shared__ unsigned int s_tk[2];
   __shared__ int s_go[2];
   unsigned int t1 = 0, t2 = 0;
@@ -449,42 +465,61 @@ persistent_kernel(PersistentArgs a) {
     if (t >= a.total) break;
     int s = 0;
     while (s + 1 < a.nstages && t >= s_first[s + 1]) ++s;
-    const long long tile = (long long)(t - s_first[s]);
+    const long long tile0 = (long long)(t - s_first[s]) * T;
+    const long long ntiles = s_st[s].n_tiles;
     if (!s_go[slot]) {
       if (threadIdx.x == 0) {
         int ok = *reinterpret_cast<volatile int*>(&a.ctl->abort) ? 0 : 1;
-        if (ok && !wait_deps(a, s_st, s_complete, s, tile)) {
-          atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
-          atomicExch(&a.ctl->abort, 1);
-          ok = 0;
+        for (int j = 0; j < T && ok && tile0 + j < ntiles; ++j) {
+          if (!wait_deps(a, s_st, s_complete, s, tile0 + j)) {
+            atomicCAS(&a.ctl->error, 0, kDevErrTimeout);
+            atomicExch(&a.ctl->abort, 1);
+            ok = 0;
+          }
         }
         s_ok = ok;
       }
       __syncthreads();
       if (!s_ok) break;
     }
-    // look ahead: the next ticket's producer counter, loaded while this tile runs
-    const unsigned int* lp = nullptr;
-    unsigned int lv = 0, ltarget = 0;
+    // look ahead (thread 0): are the next ticket's producers complete? Its answer goes to the next
+    // slot now; the loads hold back only thread 0, once per ticket.
     if (threadIdx.x == 0) {
-      t2 = atomicAdd(&a.ctl->ticket, 1u);  // needed one tile later
+      int go = 1;
       if (t1 < a.total) {
         int s1 = 0;
         while (s1 + 1 < a.nstages && t1 >= s_first[s1 + 1]) ++s1;
-        lp = dep_counter(a, s_st, s_complete, s1, (long long)(t1 - s_first[s1]), &ltarget);
-        if (lp) lv = ld_acquire(lp);
+        const long long u0 = (long long)(t1 - s_first[s1]) * T;
+        const unsigned int* lp[kMaxTicketTiles] = {nullptr, nullptr, nullptr, nullptr};
+        unsigned int lv[kMaxTicketTiles] = {0, 0, 0, 0}, lt[kMaxTicketTiles] = {0, 0, 0, 0};
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < kMaxTicketTiles; ++j)
+          if (j < T && u0 + j < s_st[s1].n_tiles) {
+            lp[j] = dep_counter(a, s_st, s_complete, s1, u0 + j, &lt[j]);
+            if (lp[j]) {
+              lv[j] = ld_relaxed(lp[j]);
+              any = true;
+            }
+          }
+        if (any) asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the loads above, then the tiles
+#pragma unroll
+        for (int j = 0; j < kMaxTicketTiles; ++j)
+          if (lp[j] && lv[j] < lt[j]) go = 0;
       }
+      t2 = atomicAdd(&a.ctl->ticket, 1u);  // needed one ticket later
+      s_tk[slot ^ 1] = t1;
+      s_go[slot ^ 1] = (t1 >= a.total || go) ? 1 : 0;
     }
     const StageDesc& d = s_st[s];
     const float2* tw = tws + s * TWB;
-    dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile, sm, tw, tw + TW2);
-    if (threadIdx.x == 0) {
-      s_tk[slot ^ 1] = t1;
-      s_go[slot ^ 1] = (t1 >= a.total || !lp || lv >= ltarget) ? 1 : 0;
+    for (int j = 0; j < T && tile0 + j < ntiles; ++j) {
+      if (j > 0) __syncthreads();  // the previous tile of the ticket is out of shared memory
+      dispatch_tile<THREADS, CODES...>(stage_code(d), d, tile0 + j, sm, tw, tw + TW2);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      signal_done(a, s_st, s, tile);
+      signal_done(a, s_st, s, tile0, (int)min((long long)T, ntiles - tile0));
       t1 = t2;
     }
   }

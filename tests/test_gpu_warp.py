@@ -26,7 +26,7 @@ def gb():
 def _pin_warp(plan, pipes=(0, 1)):
     from paper_2601_12209_gb300 import abi
     for k in pipes:
-        abi.gbfft_plan_set_tuning(plan.handle, k, False, 0xFF << 20)  # every eligible stage: warp kernel
+        abi.gbfft_plan_set_tuning(plan.handle, k, False, 0x1F << 20)  # every eligible stage: warp kernel
 
 
 @pytest.mark.parametrize("shape,slab,batch", [((512, 24, 20), False, 1), ((24, 512, 20), False, 2),
@@ -119,20 +119,21 @@ def test_persistent_launch_with_warp_body_c2c_512_cube(gb):
     n = 512
     x = synth.uniform_complex((n, n, n), seed=3)
     xd = x.cuda()
-    p = gb.Plan(n, n, n)
-    for pipe in (0, 1):
-        abi.gbfft_plan_set_tuning(p.handle, pipe, True, 0x7 << 20)
-    t = abi.gbfft_plan_get_tuning(p.handle, 0)
-    assert t["persistent"] and (t["tma_mask"] >> 20) & 0x7 == 0x7
-    y = p.forward(xd)
-    z = p.inverse(y)
     s = gb.Plan(n, n, n, staged=True)
     _pin_warp(s)
     ys = s.forward(xd)
     zs = s.inverse(ys)
-    torch.cuda.synchronize()
-    assert p.device_error() == 0
-    assert torch.equal(y, ys) and torch.equal(z, zs)
+    p = gb.Plan(n, n, n)
+    for log_t in (0, 1, 2):  # 1, 2, 4 tiles per ticket
+        for pipe in (0, 1):
+            abi.gbfft_plan_set_tuning(p.handle, pipe, True, (0x7 << 20) | (log_t << 25))
+        t = abi.gbfft_plan_get_tuning(p.handle, 0)
+        assert t["persistent"] and (t["tma_mask"] >> 20) & 0x7 == 0x7 and (t["tma_mask"] >> 25) & 0x3 == log_t
+        y = p.forward(xd)
+        z = p.inverse(y)
+        torch.cuda.synchronize()
+        assert p.device_error() == 0
+        assert torch.equal(y, ys) and torch.equal(z, zs), log_t
     e = oracle.rel_l2(y.cpu().numpy(), oracle.fft3(x.numpy()))
     e_rt = oracle.rel_l2(z.cpu().numpy(), x.numpy())
     print(f"[warp] persistent warp body c2c 512^3: fwd {e:.3e}, round trip {e_rt:.3e}")
@@ -160,3 +161,32 @@ def test_warp1024_c2c(gb, shape, slab, batch):
     e_adj = oracle.rel_l2(a.cpu().numpy(), oracle.c2c_adjoint(x.numpy()))
     print(f"[warp] 1024 {shape} slab={slab} batch={batch}: fwd {e:.3e}, round trip {e_rt:.3e}, adjoint {e_adj:.3e}")
     assert e < TOL and e_rt < TOL and e_adj < TOL
+
+
+@pytest.mark.parametrize("kind", ["c2c", "r2c"])
+def test_persistent_tiles_per_ticket_bitwise(gb, kind):
+    """Tickets of 1, 2 and 4 consecutive tiles in the persistent launch (Stockham tile bodies): the same
+    bits in every case, forward, inverse and (R2C) the five-stage Poisson pipeline; the FP64 oracle."""
+    from paper_2601_12209_gb300 import abi
+    n = 64
+    x = (synth.normal_real((2, n, n, n), seed=97) if kind == "r2c" else synth.uniform_complex((2, n, n, n), seed=97))
+    p = gb.Plan(n, n, n, kind=kind, batch=2)
+    outs = []
+    for log_t in (0, 1, 2):
+        for pipe in ((0, 1, 2) if kind == "r2c" else (0, 1)):
+            abi.gbfft_plan_set_tuning(p.handle, pipe, True, log_t << 25)
+        y = p.forward(x.cuda())
+        z = p.inverse(y)
+        ph = p.poisson(x.cuda()) if kind == "r2c" else None
+        torch.cuda.synchronize()
+        assert p.device_error() == 0
+        outs.append((y, z, ph))
+    for y, z, ph in outs[1:]:
+        assert torch.equal(y, outs[0][0]) and torch.equal(z, outs[0][1])
+        if ph is not None:
+            assert torch.equal(ph, outs[0][2])
+    ref = oracle.rfft3(x.numpy()) if kind == "r2c" else oracle.fft3(x.numpy())
+    assert oracle.rel_l2(outs[0][0].cpu().numpy(), ref) < TOL
+    assert oracle.rel_l2(outs[0][1].cpu().numpy(), x.numpy()) < TOL
+    with pytest.raises(abi.GbfftError):
+        abi.gbfft_plan_set_tuning(p.handle, 0, True, 3 << 25)  # 8 tiles per ticket: not built
