@@ -209,6 +209,18 @@ int gbfft_exec_r2r_z(gbfft_plan plan, int r2r, int inverse, const void* in, void
  * gbfft_exec_poisson_bounded.
  */
 int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out);
+/*
+ * Split gbfft_exec_host into `chunks` slabs (1 = one copy in, the transform,
+ * one copy out; 2..16) where the host array is a set of contiguous slabs: the
+ * x stage that reads the rows of the input runs on slabs of z planes, each
+ * after its slab's host-to-device copy, and the x stage that writes the rows
+ * of the output runs on slabs whose device-to-host copies start as soon as
+ * each is written; the spectrum side (read or written by the z stage, whose
+ * slabs would be strided) moves in one copy. Applies to pencil plans with
+ * natural output, batch 1, ops 0-3 (others take the one-copy path); the stages
+ * run as stage launches with the plan's tuned per-stage kernels.
+ */
+int gbfft_plan_set_host_chunks(gbfft_plan plan, int chunks);
 
 /*
  * Autotuner (Section V-B: plans pick the best execution strategy for a size

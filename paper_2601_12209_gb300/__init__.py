@@ -173,6 +173,10 @@ class Plan:
         abi.gbfft_exec_poisson_bounded(self.handle, f.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
+    def set_host_chunks(self, chunks: int) -> None:
+        """exec_host in `chunks` slabs whose copies overlap the first and last stages (1 = plain)."""
+        abi.gbfft_plan_set_host_chunks(self.handle, chunks)
+
     def exec_host(self, op: int, host_in: torch.Tensor, host_out: torch.Tensor) -> torch.Tensor:
         """End-to-end on host tensors (pinned recommended): H2D copy, op, D2H copy, wait."""
         for t in (host_in, host_out):

@@ -59,7 +59,7 @@ EXPORTED = (
     "gbfft_plan_autotune", "gbfft_plan_get_tuning", "gbfft_plan_time_stages", "gbfft_plan_stage_times",
     "gbfft_plan_set_tuning", "gbfft_many_create", "gbfft_many_layout", "gbfft_many_exec",
     "gbfft_many_exec_separate", "gbfft_many_get_device_error", "gbfft_many_destroy", "gbfft_many_exec_staged",
-    "gbfft_many_autotune", "gbfft_many_get_tuning", "gbfft_many_set_tuning", "gbfft_many_get_lag",
+    "gbfft_plan_set_host_chunks", "gbfft_many_autotune", "gbfft_many_get_tuning", "gbfft_many_set_tuning", "gbfft_many_get_lag",
     "gbfft_many_set_lag",
 )
 
@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
             "gbfft_plan_set_tuning": (i, [vp, i, i, u]),
             "gbfft_many_create": (i, [plan_p, i, ctypes.POINTER(i), i, i, u]),
             "gbfft_many_autotune": (i, [vp, vp]),
+            "gbfft_plan_set_host_chunks": (i, [vp, i]),
             "gbfft_many_get_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), i, ctypes.POINTER(i),
                                           ctypes.POINTER(ctypes.c_float)]),
             "gbfft_many_set_tuning": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), i]),
@@ -300,6 +301,10 @@ def gbfft_many_create(shapes, flags: int = 0, kind: int = GBFFT_C2C, dtype: int 
     h = ctypes.c_void_p()
     _call("gbfft_many_create", ctypes.byref(h), len(shapes), dims, int(kind), int(dtype), int(flags))
     return h.value
+
+
+def gbfft_plan_set_host_chunks(plan: int, chunks: int) -> None:
+    _call("gbfft_plan_set_host_chunks", ctypes.c_void_p(plan), int(chunks))
 
 
 def gbfft_many_autotune(m: int, stream: int = 0) -> None:

@@ -298,6 +298,11 @@ struct gbfft_plan_s {
   void* h_out_dev = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
   cudaStream_t h_stream = nullptr;
+  // chunked host-buffer execution: slabs of the first and last stages, their copies on h_stream, the
+  // stages on h_stream2, ordered by events
+  int host_chunks = 1;
+  cudaStream_t h_stream2 = nullptr;
+  cudaEvent_t h_ev[32] = {};
   // autotuned launch choice per pipeline (forward, inverse, Poisson)
   struct Tuning {
     bool tuned = false;
@@ -1055,6 +1060,9 @@ static void free_plan(gbfft_plan_s* p) {
   cudaFree(p->tw4_y);
   cudaFree(p->tw4_z);
   if (p->h_stream) cudaStreamDestroy(p->h_stream);
+  if (p->h_stream2) cudaStreamDestroy(p->h_stream2);
+  for (cudaEvent_t e : p->h_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& c : p->timed)
     for (int k = 0; k < c.nev; ++k) cudaEventDestroy(c.ev[k]);
   delete p;
@@ -1347,6 +1355,127 @@ static size_t op_out_bytes(const gbfft_plan_s* p, int op) {
   return real_b;
 }
 
+// The part of stage d's array on one side for outer indices [o0, o1) of a
+// one-batch stage, as a 2D region of `rows` rows of `width` bytes at `pitch`
+// (element offset `off`); false if the outer blocks are not contiguous there.
+static bool outer_region(long long o_stride, long long g_stride, long long n_stride, int n_group, int n_len,
+                         int mode, long long o0, long long o1, long long* off, size_t* width, size_t* pitch,
+                         size_t* rows) {
+  if ((long long)n_group * g_stride != o_stride) return false;
+  if (mode == kRow) {
+    if (n_stride != 1) return false;
+    *off = o0 * o_stride;
+    *width = (size_t)((o1 - o0) * o_stride) * sizeof(float2);
+    *pitch = *width;
+    *rows = 1;
+    return true;
+  }
+  if (g_stride != 1) return false;
+  *off = o0 * o_stride;
+  *width = (size_t)((o1 - o0) * o_stride) * sizeof(float2);
+  *pitch = (size_t)n_stride * sizeof(float2);
+  *rows = (size_t)n_len;
+  return true;
+}
+
+static cudaError_t copy_region(void* dst, const void* src, long long off, size_t width, size_t pitch, size_t rows,
+                               cudaMemcpyKind kind, cudaStream_t s) {
+  const char* sp = reinterpret_cast<const char*>(src) + off * (long long)sizeof(float2);
+  char* dp = reinterpret_cast<char*>(dst) + off * (long long)sizeof(float2);
+  if (rows == 1 || width == pitch) return cudaMemcpyAsync(dp, sp, width * rows, kind, s);
+  return cudaMemcpy2DAsync(dp, pitch, sp, pitch, width, rows, kind, s);
+}
+
+// Host-buffer execution with the copies overlapped with the first and last
+// stages: a first stage that reads rows runs on K slabs of its outer axis,
+// each after its slab's host-to-device copy; a last stage that writes rows
+// runs on K slabs, and each slab's device-to-host copy starts as soon as the
+// slab is written (the column sides, whose slabs would be strided, move in
+// one copy). Pencil plans
+// with natural output, one batch entry, ops 0-3; the stages run as staged
+// launches with the plan's tuned per-stage kernels. Returns 1 when the plan
+// or op does not qualify (the caller takes the plain path).
+static int exec_host_chunked(gbfft_plan_s* p, int op, const void* hin, void* hout, int K) {
+  if (is_slab(p) || (p->flags & GBFFT_TRANSPOSED_OUT) || p->batch != 1 || op < 0 || op > 3) return 1;
+  const int pipe = pipe_of(op);
+  const long long cap_in = (long long)(p->h_in_bytes / sizeof(float2));
+  int rc = ensure_workspace(p);
+  if (rc) return rc;
+  Pipeline P = build_pipeline(p, pipe, op, Buf{p->h_in_dev, cap_in}, Buf{p->h_out_dev, cap_in}, ws_buf(p, 0),
+                              ws_buf(p, 1));
+  if (P.n != 3) return 1;
+  rc = validate(P);
+  if (rc) return rc;
+  const StageDesc& a = P.st[0];
+  const StageDesc& z = P.st[2];
+  if (a.batch != 1 || z.batch != 1) return 1;
+  // the per-stage kernel choice of the plan's tuning (staged), else the staged defaults
+  const gbfft_plan_s::Tuning& t = p->tune[pipe];
+  const bool use_t = t.tuned && !t.persistent && !t.plane_mask;
+  unsigned f[3];
+  for (int s = 0; s < 3; ++s) {
+    const bool tma = use_t ? ((t.tma_mask >> s) & 1u) : !(p->flags & GBFFT_NO_TMA);
+    f[s] = (tma ? 0u : GBFFT_NO_TMA) | (use_t && ((t.warp_mask >> s) & 1u) ? kUseWarpKernel : 0u) |
+           (use_t && ((t.prefetch_mask >> s) & 1u) ? kUsePrefetchKernel : 0u);
+  }
+  // slabs only where they are contiguous (the row side: the real or natural rows of the x stage); a
+  // column side (the natural spectrum of the z stage) moves in one copy -- its slabs would be strided 2D
+  // copies, measured slower than one contiguous copy
+  const int ka = a.in_mode == kRow ? std::min<int>(K, a.n_outer) : 1;
+  const int kz = z.out_mode == kRow ? std::min<int>(K, z.n_outer) : 1;
+  long long off;
+  size_t w, pitch, rows;
+  // the slabs of the first stage's input and the last stage's output must be contiguous or 2D regions
+  if (!outer_region(a.in_o, a.in_g, a.in_n, a.n_group, a.n_in, a.in_mode, 0, 1, &off, &w, &pitch, &rows) ||
+      !outer_region(z.out_o, z.out_g, z.out_n, z.n_group, z.n_out, z.out_mode, 0, 1, &off, &w, &pitch, &rows))
+    return 1;
+  if (!p->h_stream2 && cudaStreamCreateWithFlags(&p->h_stream2, cudaStreamNonBlocking) != cudaSuccess)
+    return GBFFT_ERR_CUDA;
+  for (cudaEvent_t& e : p->h_ev)
+    if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return GBFFT_ERR_CUDA;
+  cudaStream_t cs = p->h_stream, ks = p->h_stream2;
+  int* err = &p->ctl->error;
+  // first stage: slab k after its copy
+  for (int k = 0; k < ka; ++k) {
+    const long long o0 = (long long)a.n_outer * k / ka, o1 = (long long)a.n_outer * (k + 1) / ka;
+    outer_region(a.in_o, a.in_g, a.in_n, a.n_group, a.n_in, a.in_mode, o0, o1, &off, &w, &pitch, &rows);
+    if (copy_region(p->h_in_dev, hin, off, w, pitch, rows, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(p->h_ev[k], cs) != cudaSuccess || cudaStreamWaitEvent(ks, p->h_ev[k], 0) != cudaSuccess)
+      return GBFFT_ERR_CUDA;
+    StageDesc d = a;
+    d.in += o0 * a.in_o;
+    d.out += o0 * a.out_o;
+    d.n_outer = (int)(o1 - o0);
+    d.n_tiles = (long long)d.n_outer * d.n_gchunks;
+    rc = launch_stage(d, ks, f[0], err);
+    if (rc) return rc;
+  }
+  rc = launch_stage(P.st[1], ks, f[1], err);
+  if (rc) return rc;
+  // last stage: slab k, then its copy
+  for (int k = 0; k < kz; ++k) {
+    const long long o0 = (long long)z.n_outer * k / kz, o1 = (long long)z.n_outer * (k + 1) / kz;
+    StageDesc d = z;
+    d.in += o0 * z.in_o;
+    d.out += o0 * z.out_o;
+    d.n_outer = (int)(o1 - o0);
+    d.n_tiles = (long long)d.n_outer * d.n_gchunks;
+    rc = launch_stage(d, ks, f[2], err);
+    if (rc) return rc;
+    outer_region(z.out_o, z.out_g, z.out_n, z.n_group, z.n_out, z.out_mode, o0, o1, &off, &w, &pitch, &rows);
+    if (cudaEventRecord(p->h_ev[16 + k], ks) != cudaSuccess || cudaStreamWaitEvent(cs, p->h_ev[16 + k], 0) != cudaSuccess ||
+        copy_region(hout, p->h_out_dev, off, w, pitch, rows, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      return GBFFT_ERR_CUDA;
+  }
+  return cuda_err(cudaStreamSynchronize(cs));
+}
+
+int gbfft_plan_set_host_chunks(gbfft_plan plan, int chunks) {
+  if (!plan || chunks < 1 || chunks > 16) return GBFFT_ERR_INVALID_ARG;
+  plan->host_chunks = chunks;
+  return GBFFT_OK;
+}
+
 int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out) {
   if (!plan || !host_in || !host_out) return GBFFT_ERR_INVALID_ARG;
   if (op < 0 || op > 5) return GBFFT_ERR_INVALID_ARG;
@@ -1361,6 +1490,10 @@ int gbfft_exec_host(gbfft_plan plan, int op, const void* host_in, void* host_out
       return GBFFT_ERR_ALLOC;
     }
     plan->h_in_bytes = plan->h_out_bytes = big;
+  }
+  if (plan->host_chunks > 1) {
+    const int crc = exec_host_chunked(plan, op, host_in, host_out, plan->host_chunks);
+    if (crc != 1) return crc;
   }
   cudaStream_t s = plan->h_stream;
   if (cudaMemcpyAsync(plan->h_in_dev, host_in, ib, cudaMemcpyHostToDevice, s) != cudaSuccess)

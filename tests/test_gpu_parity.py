@@ -411,3 +411,50 @@ def test_graph_capture_of_staged_launches(gb):
     assert p.device_error() == 0
     assert torch.equal(s2, spec) and torch.equal(b2, back)
     assert err("graph-captured r2c", s2.cpu().numpy(), oracle.rfft3(r.cpu().numpy())) < TOL
+
+
+@pytest.mark.parametrize("kind,shape,tune", [("r2c", (64, 48, 40), False), ("c2c", (30, 20, 16), False),
+                                             ("r2c", (512, 48, 24), True), ("c2c", (64, 96, 3), False)],
+                         ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+def test_exec_host_chunked(gb, kind, shape, tune):
+    """Host buffers in slabs whose copies overlap the first and last stages (contiguous z slabs on the real /
+    natural side of x, strided y slabs on the spectrum side of z): the bits of the one-copy path for ops 0-3
+    with the same stage kernels, for slab counts that do and do not divide the axes (more slabs than an axis
+    has entries included), pinned and pageable buffers; the FP64 oracle."""
+    from paper_2601_12209_gb300 import abi
+    nx, ny, nz = shape
+    p = gb.Plan(nx, ny, nz, kind=kind)
+    if tune:
+        p.autotune()
+    else:
+        for pipe in (0, 1):
+            abi.gbfft_plan_set_tuning(p.handle, pipe, False, 0)  # staged thread-load launches
+    r2c = kind == "r2c"
+    src = synth.normal_real((nz, ny, nx), seed=54) if r2c else synth.uniform_complex((nz, ny, nx), seed=54)
+    spec = p.forward(src.to(dev())).cpu()
+    for op, hin in ((abi.GBFFT_OP_FORWARD, src), (abi.GBFFT_OP_INVERSE, spec), (abi.GBFFT_OP_ADJOINT, spec),
+                    (abi.GBFFT_OP_INVERSE_ADJOINT, src)):
+        outs = []
+        for chunks in (1, 3, 7, 16):
+            p.set_host_chunks(chunks)
+            for pinned in (True, False):
+                h_in = hin.contiguous().pin_memory() if pinned else hin.contiguous().clone()
+                shape_out = spec.shape if op in (abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE_ADJOINT) else src.shape
+                dt = spec.dtype if op in (abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE_ADJOINT) else src.dtype
+                h_out = torch.empty(shape_out, dtype=dt)
+                h_out = h_out.pin_memory() if pinned else h_out
+                p.exec_host(op, h_in, h_out)
+                outs.append(h_out)
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0]), (kind, shape, op)
+    p.set_host_chunks(8)
+    h_out = torch.empty(spec.shape, dtype=spec.dtype).pin_memory()
+    p.exec_host(abi.GBFFT_OP_FORWARD, src.pin_memory(), h_out)
+    ref = oracle.rfft3(src.numpy()) if r2c else oracle.fft3(src.numpy())
+    assert err(f"exec_host chunked {kind} {shape}", h_out.numpy(), ref) < TOL
+    back = torch.empty(src.shape, dtype=src.dtype).pin_memory()
+    p.exec_host(abi.GBFFT_OP_INVERSE, h_out, back)
+    assert err(f"exec_host chunked round trip {kind} {shape}", back.numpy(), src.numpy()) < TOL
+    with pytest.raises(abi.GbfftError):
+        p.set_host_chunks(17)
+    assert p.device_error() == 0
