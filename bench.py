@@ -308,7 +308,8 @@ def main():
                          "staged_c2c, staged_lsu_c2c, persistent_c2c, slab_c2c, slab_r2c; or split_fp16_1024, "
                          "split_bf16_1024, split_fp16_tc5_1024, split_bf16_tc5_1024, split_fp32_1024 (C2C "
                          "1024x512x64, staged thread-load launches; tensor-core radix-16 passes unless fp32); "
-                         "or pinned_r2c:<fwd bits>:<inv bits>, persistent_warp_c2c (C2C 512^3, one persistent "
+                         "or pinned_r2c:<fwd bits>:<inv bits> (pinned_slab_r2c: slab plan), dsm_slab_r2c (R2C 512x512x128 slab, "
+                         "plane launches in distributed shared memory), persistent_warp_c2c (C2C 512^3, one persistent "
                          "launch with warp-per-pencil tile bodies), warp1024_c2c (C2C 1024x512x64, warp-per-pencil "
                          "stages)")
     args = ap.parse_args()
@@ -530,12 +531,21 @@ def ncu_case(name):
         for k in (0, 1):
             abi.gbfft_plan_set_tuning(plan.handle, k, False, 0x1F << 20)
         x = synth.uniform_complex((64, 512, 1024), seed=3).cuda()
-    elif name.startswith("pinned_r2c"):
+    elif name == "dsm_slab_r2c":
+        # R2C 512 x 512 x 128 slab (128 MiB real in, 135 MB spectrum out): the in-plane pairs as plane launches
+        # with the intermediate in distributed shared memory
+        kind = "r2c"
+        plan = gb.Plan(N, N, 128, kind=kind, slab=True)
+        abi.gbfft_plan_set_tuning(plan.handle, 0, False, (1 << 27) | (1 << 8))
+        abi.gbfft_plan_set_tuning(plan.handle, 1, False, (1 << 27) | (2 << 8))
+        x = synth.normal_real((128, N, N), seed=2).cuda()
+    elif name.startswith("pinned_r2c") or name.startswith("pinned_slab_r2c"):
         # pinned_r2c:<forward bits>:<inverse bits>: R2C 512^3 with a fixed launch choice (the tuning bits of
-        # gbfft_plan_set_tuning), e.g. the benchmark's autotuned choice, so a profile sees the timed kernels
+        # gbfft_plan_set_tuning), e.g. the benchmark's autotuned choice, so a profile sees the timed kernels;
+        # pinned_slab_r2c: the same for a slab plan
         _, fwd, inv = name.split(":")
         kind = "r2c"
-        plan = gb.Plan(N, N, N, kind=kind)
+        plan = gb.Plan(N, N, N, kind=kind, slab=name.startswith("pinned_slab"))
         abi.gbfft_plan_set_tuning(plan.handle, 0, False, int(fwd, 0))
         abi.gbfft_plan_set_tuning(plan.handle, 1, False, int(inv, 0))
         x = synth.normal_real((N, N, N), seed=2).cuda()
@@ -762,6 +772,29 @@ def extra_variants(torch, gb, abi, dev, stream, steps, warmup):
         fused[f"cluster_{cx}"] = {"fwd_ms": med[0], "inv_ms": med[1]}
         p.close()
     out["r2c_512_slab_fused_plane"] = fused
+    # the in-plane pairs as plane launches that keep each plane's intermediate in distributed shared memory
+    # (8-CTA clusters): two HBM passes per transform
+    p = gb.Plan(N, N, N, kind="r2c", slab=True)
+    abi.gbfft_plan_set_tuning(p.handle, 0, False, (1 << 27) | (1 << 8))  # x,y in one launch; z
+    abi.gbfft_plan_set_tuning(p.handle, 1, False, (1 << 27) | (2 << 8))  # z; y,x in one launch
+    med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_INVERSE], steps, warmup, stream)
+    abi.gbfft_plan_time_stages(p.handle, True)
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            p.inverse(p.forward(r, stream=stream), stream=stream)
+    torch.cuda.synchronize()
+    abi.gbfft_plan_time_stages(p.handle, False)
+    seg_f, _ = abi.gbfft_plan_stage_times(p.handle, 0)
+    seg_i, _ = abi.gbfft_plan_stage_times(p.handle, 1)
+    pair_bytes = N * N * N * 4 + N * N * (N // 2 + 1) * 8  # real plane in, half spectrum out (or back)
+    out["r2c_512_slab_dsm"] = {
+        "fwd_ms": med[0], "inv_ms": med[1], "fwd_inv_ms": med[0] + med[1],
+        "alg_gbs": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9,
+        "frac": 2 * b / ((med[0] + med[1]) * 1e-3) / 1e9 / measured_peaks()[0],
+        "launch_ms": {"forward": seg_f, "inverse": seg_i},
+        "plane_launch_alg_gbs": [pair_bytes / (seg_f[0] * 1e-3) / 1e9 if seg_f else None,
+                                 pair_bytes / (seg_i[1] * 1e-3) / 1e9 if len(seg_i) > 1 else None]}
+    p.close()
     p = gb.Plan(N, N, N, kind="r2c")
     med, _ = time_variant(torch, p, r, [abi.GBFFT_OP_FORWARD, abi.GBFFT_OP_ADJOINT], steps, warmup, stream)
     out["r2c_512_fwd_adjoint_ms"] = med[0] + med[1]

@@ -233,7 +233,9 @@ int gbfft_plan_set_host_chunks(gbfft_plan plan, int chunks);
  * kernel family exists; with 1, 2 or 4 consecutive tiles per ticket, and also
  * with the warp-per-pencil tile body on its length-512 complex stages) and, for slab plans, each in-plane stage pair as
  * one fused plane launch (a thread-block cluster per xy-plane runs both
- * stages while the plane is in L2); it keeps the fastest. Later exec calls
+ * stages while the plane is in L2, or, for real transforms of 512-point rows
+ * with ny = 256 or 512, an 8-CTA cluster per plane keeps the plane's
+ * intermediate in distributed shared memory); it keeps the fastest. Later exec calls
  * use the choice. Blocking (synchronises `stream`); allocates the plan's
  * workspace and two scratch buffers on first use; respects GBFFT_STAGED and
  * GBFFT_NO_TMA. Do not call it during stream capture.
@@ -249,7 +251,9 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream);
  * *persistent = 1: stage s of the persistent launch runs the warp-per-pencil
  * tile body (length-512 complex stages of 512-thread families) --, bits
  * 25-26 = log2 of the persistent launch's tiles per ticket (1, 2, 4), bit
- * 28 + s (s < 4) = stage s runs the C2R kernel with cp.async prefetch; *ms =
+ * 27 = the fused plane launches keep the intermediate in distributed shared
+ * memory (where that kernel is built; others go through L2), bit 28 + s
+ * (s < 4) = stage s runs the C2R kernel with cp.async prefetch; *ms =
  * measured time of the choice, stage_ms[0..4] = per-stage times of the staged
  * candidates. Any output pointer may be NULL.
  */
@@ -264,8 +268,10 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
  * kernel for stage s (where it applies), bit 8 + s fusing stages s and s+1
  * into one plane launch (where they are a slab plan's in-plane pair), bits
  * 16-19 the CTAs per plane cluster (2, 4 or 8; 0 = by plane size), bit 20 + s
- * the warp-per-pencil kernel for stage s (where it is built) and bit 28 + s
- * the C2R prefetch kernel for stage s (where it applies).
+ * the warp-per-pencil kernel for stage s (where it is built), bit 27 the
+ * plane launches with the intermediate in distributed shared memory (real
+ * transforms of 512-point rows, ny = 256 or 512; 8 CTAs per plane) and bit
+ * 28 + s the C2R prefetch kernel for stage s (where it applies).
  */
 int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigned tma_mask);
 /*

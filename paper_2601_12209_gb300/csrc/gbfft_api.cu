@@ -17,6 +17,7 @@
 #include "gbfft_kernels.cuh"
 #include "gbfft_many.cuh"
 #include "gbfft_plane.cuh"
+#include "gbfft_plane_dsm.cuh"
 #include "gbfft_prefetch.cuh"
 #include "gbfft_warp.cuh"
 
@@ -42,6 +43,7 @@ void register_tma_group_0(std::vector<TmaKernel>&);
 void register_tma_group_1(std::vector<TmaKernel>&);
 void register_tma_group_2(std::vector<TmaKernel>&);
 void register_plane_group_0(std::vector<PlaneKernel>&);
+void register_plane_dsm_group_0(std::vector<PlaneDsmKernel>&);
 void register_warp_group_0(std::vector<WarpKernel>&);
 void register_warp_group_1(std::vector<WarpKernel>&);
 void register_prefetch_group_0(std::vector<PrefetchKernel>&);
@@ -57,6 +59,10 @@ std::vector<WarpKernel>& warp_registry() {
 }
 std::vector<PlaneKernel>& plane_registry() {
   static std::vector<PlaneKernel> v;
+  return v;
+}
+std::vector<PlaneDsmKernel>& plane_dsm_registry() {
+  static std::vector<PlaneDsmKernel> v;
   return v;
 }
 std::vector<StageKernel>& stage_registry() {
@@ -98,6 +104,7 @@ static void ensure_registry() {
     register_tma_group_1(t);
     register_tma_group_2(t);
     register_plane_group_0(plane_registry());
+    register_plane_dsm_group_0(plane_dsm_registry());
     register_warp_group_0(warp_registry());
     register_warp_group_1(warp_registry());
     register_prefetch_group_0(prefetch_registry());
@@ -313,6 +320,7 @@ struct gbfft_plan_s {
     unsigned prefetch_mask = 0;  // bit s: stage s runs the cp.async prefetch C2R kernel
     int persistent_tiles = 1;    // persistent launch: consecutive tiles per ticket (1, 2, 4)
     int plane_cx = 0;         // CTAs per plane cluster of the fused launches (0: by plane size)
+    bool plane_dsm = false;   // fused plane launches keep the intermediate in distributed shared memory
     float ms = 0.f;         // measured time of the chosen launch(es)
     float stage_ms[kMaxStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
   } tune[3];
@@ -842,11 +850,40 @@ static const PlaneKernel* find_plane(const Pipeline& P, int s) {
   return nullptr;
 }
 
+// The plane kernel with the intermediate in distributed shared memory for
+// stages s and s+1: a real transform's in-plane pair (forward: the R2C x stage
+// of 512-point rows, then y; inverse: y, then the C2R x stage) with contiguous
+// rows, the y side in the natural spectrum layout, FP32, and a built length ny.
+static const PlaneDsmKernel* find_plane_dsm(const Pipeline& P, int s) {
+  if (s + 1 >= P.n) return nullptr;
+  const StageDesc& a = P.st[s];
+  const StageDesc& b = P.st[s + 1];
+  if (b.dep_rule != kDepOuter || a.batch != b.batch || a.n_outer != b.n_outer || a.dir != b.dir) return nullptr;
+  if (a.prec != kPrecFP32 || b.prec != kPrecFP32 || a.n_tiles == 0 || b.n_tiles == 0) return nullptr;
+  if (a.m_split != 0 || b.m_split != 0) return nullptr;
+  const bool fwd = a.dir < 0;
+  const StageDesc& x = fwd ? a : b;
+  const StageDesc& y = fwd ? b : a;
+  if (x.kind != (fwd ? kR2CPost : kC2RPre) || x.L != kDsmM || y.kind != kPlain) return nullptr;
+  if (!x.twn || !x.tw2 || !y.twn || x.n_group != y.L || y.n_group != kDsmM + 1) return nullptr;
+  if (fwd) {
+    if (x.in_mode != kRow || x.in_n != 1 || x.scale != 1.f) return nullptr;
+    if (y.out_mode != kCol || y.out_g != 1 || y.out_n != kDsmM + 1) return nullptr;
+  } else {
+    if (x.out_mode != kRow || x.out_n != 1) return nullptr;
+    if (y.in_mode != kCol || y.in_g != 1 || y.in_n != kDsmM + 1) return nullptr;
+  }
+  ensure_registry();
+  for (const auto& k : plane_dsm_registry())
+    if (k.ny == y.L && k.dir == a.dir) return &k;
+  return nullptr;
+}
+
 // Bit s set for every stage s that starts a fusable in-plane pair.
 static unsigned plane_mask_of(const Pipeline& P) {
   unsigned m = 0;
   for (int s = 0; s + 1 < P.n; ++s)
-    if (find_plane(P, s)) {
+    if (find_plane(P, s) || find_plane_dsm(P, s)) {
       m |= 1u << s;
       ++s;
     }
@@ -884,14 +921,67 @@ static int launch_plane(const PlaneKernel* k, const StageDesc& a, const StageDes
   return cuda_err(cudaLaunchKernelExC(&cfg, k->fn, args));
 }
 
+// Clusters of kDsmCta CTAs (one per SM: each holds 1/8 of a plane), as many as
+// fit on the GPU at once, each running planes c, c + clusters, ...
+static std::map<std::pair<int, const void*>, int> g_dsm_clusters;
+static int launch_plane_dsm(const PlaneDsmKernel* k, const StageDesc& a, const StageDesc& b, cudaStream_t stream) {
+  const long long planes = (long long)a.batch * a.n_outer;
+  int bpsm = 1;
+  cudaError_t e = launch_info(k->fn, k->threads, k->smem, &bpsm);
+  if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.blockDim = dim3((unsigned)k->threads);
+  cfg.dynamicSmemBytes = k->smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)kDsmCta;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GBFFT_ERR_CUDA;
+  int clusters = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_dsm_clusters.find({dev, k->fn});
+    if (it != g_dsm_clusters.end()) {
+      clusters = it->second;
+    } else {
+      cfg.gridDim = dim3((unsigned)kDsmCta);
+      if (cudaOccupancyMaxActiveClusters(&clusters, k->fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return GBFFT_ERR_CUDA;
+      }
+      g_dsm_clusters[{dev, k->fn}] = clusters;
+    }
+  }
+  if (clusters < 1) return GBFFT_ERR_UNSUPPORTED_SIZE;
+  cfg.gridDim = dim3((unsigned)(std::min<long long>(planes, clusters) * kDsmCta));
+  StageDesc da = a, db = b;
+  void* args[] = {&da, &db};
+  return cuda_err(cudaLaunchKernelExC(&cfg, k->fn, args));
+}
+
 // Staged launches with an explicit per-stage kernel choice (bit s of tma_mask:
 // tensor-copy kernel for stage s when it can run there; bit s of plane_mask:
 // stages s and s+1 as one fused plane launch when they form an in-plane pair).
 static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cudaStream_t stream, int pipe,
-                      unsigned plane_mask = 0, int plane_cx = 0, unsigned warp_mask = 0, unsigned prefetch_mask = 0) {
+                      unsigned plane_mask = 0, int plane_cx = 0, unsigned warp_mask = 0, unsigned prefetch_mask = 0,
+                      bool plane_dsm = false) {
   record_event(p, stream, pipe, true);
   for (int s = 0; s < P.n; ++s) {
     if ((plane_mask >> s) & 1u) {
+      const PlaneDsmKernel* kd = plane_dsm ? find_plane_dsm(P, s) : nullptr;
+      if (kd) {
+        int rc = launch_plane_dsm(kd, P.st[s], P.st[s + 1], stream);
+        if (rc) return rc;
+        record_event(p, stream, pipe, false);
+        ++s;
+        continue;
+      }
       if (const PlaneKernel* k = find_plane(P, s)) {
         int rc = launch_plane(k, P.st[s], P.st[s + 1], stream, plane_cx);
         if (rc) return rc;
@@ -921,7 +1011,8 @@ static int run_pipeline(gbfft_plan_s* p, const Pipeline& P, int pipe, cudaStream
       return rc;
     }
     const gbfft_plan_s::Tuning& t = p->tune[pipe];
-    return run_staged(p, P, t.tma_mask, stream, pipe, t.plane_mask, t.plane_cx, t.warp_mask, t.prefetch_mask);
+    return run_staged(p, P, t.tma_mask, stream, pipe, t.plane_mask, t.plane_cx, t.warp_mask, t.prefetch_mask,
+                      t.plane_dsm);
   }
   const bool staged = (p->flags & GBFFT_STAGED) != 0;
   const unsigned tm = (p->flags & GBFFT_NO_TMA) ? 0u : 0xFFu;
@@ -1674,12 +1765,21 @@ int gbfft_plan_autotune(gbfft_plan plan, void* stream) {
     }
     const unsigned pm = (plan->flags & GBFFT_STAGED) ? 0u : plane_mask_of(P);
     if (pm) {
-      for (int cx : {2, 4, 8}) {
-        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx, wm, qm); }, st, reps);
+      // cluster plane launches through L2 (2, 4 or 8 CTAs per plane), then with the intermediate in
+      // distributed shared memory (cx = 0 marks that candidate)
+      for (int cx : {2, 4, 8, 0}) {
+        const bool dsm = cx == 0;
+        if (dsm) {
+          bool any = false;
+          for (int s = 0; s + 1 < P.n; ++s) any = any || (((pm >> s) & 1u) && find_plane_dsm(P, s));
+          if (!any) continue;
+        }
+        float tf = time_calls([&] { return run_staged(plan, P, tm, st, pipe, pm, cx, wm, qm, dsm); }, st, reps);
         if (tf >= 0.f && tf < t.ms) {
           t.persistent = false;
           t.plane_mask = pm;
           t.plane_cx = cx;
+          t.plane_dsm = dsm;
           t.ms = tf;
           t.tma_mask = tm;
           t.warp_mask = wm;
@@ -1703,7 +1803,7 @@ int gbfft_plan_get_tuning(gbfft_plan plan, int pipeline, int* tuned, int* persis
   if (tma_mask)
     *tma_mask = (t.tma_mask & 0xFFu) | ((t.plane_mask & 0xFFu) << 8) | ((unsigned)(t.plane_cx & 0xF) << 16) |
                 ((t.warp_mask & 0x1Fu) << 20) | ((unsigned)(t.persistent_tiles == 4 ? 2 : t.persistent_tiles == 2 ? 1 : 0) << 25) |
-                ((t.prefetch_mask & 0xFu) << 28);
+                ((t.plane_dsm ? 1u : 0u) << 27) | ((t.prefetch_mask & 0xFu) << 28);
   if (ms) *ms = t.ms;
   if (stage_ms)
     for (int s = 0; s < kMaxStages; ++s) stage_ms[s] = t.stage_ms[s];
@@ -1722,6 +1822,7 @@ int gbfft_plan_set_tuning(gbfft_plan plan, int pipeline, int persistent, unsigne
   t.warp_mask = (tma_mask >> 20) & 0x1Fu;
   t.persistent_tiles = 1 << ((tma_mask >> 25) & 0x3u);
   t.prefetch_mask = (tma_mask >> 28) & 0xFu;
+  t.plane_dsm = ((tma_mask >> 27) & 1u) != 0;
   t.ms = 0.f;
   for (int s = 0; s < kMaxStages; ++s) t.stage_ms[s] = 0.f;
   return GBFFT_OK;
