@@ -74,7 +74,7 @@ def measured_peaks():
 
 # the sources of the stage, tensor-copy and warp-per-pencil kernels' device code
 KERNEL_SOURCES = ("gbfft_internal.h", "gbfft_device.cuh", "gbfft_kernels.cuh", "gbfft_tma.cuh", "gbfft_warp.cuh",
-                  "gbfft_prefetch.cuh")
+                  "gbfft_warp_tile.cuh", "gbfft_prefetch.cuh")
 # ... and of the fused plane kernels
 PLANE_SOURCES = KERNEL_SOURCES + ("gbfft_plane.cuh",)
 

@@ -57,6 +57,7 @@ std::vector<WarpKernel>& warp_registry() {
   static std::vector<WarpKernel> v;
   return v;
 }
+
 std::vector<PlaneKernel>& plane_registry() {
   static std::vector<PlaneKernel> v;
   return v;
@@ -656,6 +657,12 @@ constexpr unsigned kUseWarpKernel = 1u << 30;
 // (column-side half spectrum in, real rows out; FP32).
 constexpr unsigned kUsePrefetchKernel = 1u << 29;
 
+// Launch flags of a stage from its tuning bits (tensor-copy, warp-per-pencil,
+// C2R prefetch kernel).
+static unsigned stage_flags(bool tma, bool warp, bool prefetch) {
+  return (tma ? 0u : GBFFT_NO_TMA) | (warp ? kUseWarpKernel : 0u) | (prefetch ? kUsePrefetchKernel : 0u);
+}
+
 static const PrefetchKernel* find_prefetch(const StageDesc& d) {
   if (d.prec != kPrecFP32 || d.kind != kC2RPre || d.dir < 0 || !d.tw2) return nullptr;
   if (d.in_mode != kCol || d.out_mode != kRow || static_cast<const void*>(d.in) == static_cast<const void*>(d.out))
@@ -990,8 +997,7 @@ static int run_staged(gbfft_plan_s* p, const Pipeline& P, unsigned tma_mask, cud
         continue;
       }
     }
-    const unsigned f = (((tma_mask >> s) & 1u) ? 0u : GBFFT_NO_TMA) | (((warp_mask >> s) & 1u) ? kUseWarpKernel : 0u) |
-                       (((prefetch_mask >> s) & 1u) ? kUsePrefetchKernel : 0u);
+    const unsigned f = stage_flags((tma_mask >> s) & 1u, (warp_mask >> s) & 1u, (prefetch_mask >> s) & 1u);
     int rc = launch_stage(P.st[s], stream, f, &p->ctl->error);
     if (rc) return rc;
     record_event(p, stream, pipe, false);
@@ -1506,8 +1512,7 @@ static int exec_host_chunked(gbfft_plan_s* p, int op, const void* hin, void* hou
   unsigned f[3];
   for (int s = 0; s < 3; ++s) {
     const bool tma = use_t ? ((t.tma_mask >> s) & 1u) : !(p->flags & GBFFT_NO_TMA);
-    f[s] = (tma ? 0u : GBFFT_NO_TMA) | (use_t && ((t.warp_mask >> s) & 1u) ? kUseWarpKernel : 0u) |
-           (use_t && ((t.prefetch_mask >> s) & 1u) ? kUsePrefetchKernel : 0u);
+    f[s] = stage_flags(tma, use_t && ((t.warp_mask >> s) & 1u), use_t && ((t.prefetch_mask >> s) & 1u));
   }
   // slabs only where they are contiguous (the row side: the real or natural rows of the x stage); a
   // column side (the natural spectrum of the z stage) moves in one copy -- its slabs would be strided 2D

@@ -134,7 +134,8 @@ __device__ __forceinline__ void warp_dft(float2 (&v)[R], const float2* w32) {
 }
 
 // Steps 1 and 2 on lane t's values x[t + 32 i] (i < R1), then the transpose
-// write: y_t[k1] lands in wr[k1 * P + t].
+// write: y_t[k1] lands in wr[k1 * P + t]. (warp_tile below spells these steps
+// out in place: the same arithmetic, kept inline where the stage kernels run it.)
 template <int L, int DIR>
 __device__ __forceinline__ void warp_steps12(float2 (&v)[WarpGeom<L>::R1], float2* wr, const float2* tws,
                                              const float2* w32, int t) {
@@ -189,7 +190,8 @@ template <int L, int DIR, int KIND>
 __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, float2* sm, const float2* tws,
                                           const float2* w32, const float2* tw2) {
   using G = WarpGeom<L>;
-  constexpr int R1 = G::R1, C = G::C, RG = G::kRegion;
+  constexpr int R1 = G::R1, C = G::C, P = G::kPitch, RG = G::kRegion;
+  constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
   const int k1 = lane / C, c = lane % C;
   const int m = C == 2 ? c : ((c >> 1) + 2 * (c & 1));  // output block of this lane after step 5
@@ -226,7 +228,11 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
       for (int i = 0; i < R1; ++i)
         v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
     }
-    warp_steps12<L, DIR>(v, wr, tws, w32, lane);
+    warp_dft<R1, DIR>(v, w32);
+#pragma unroll
+    for (int k = 1; k < R1; ++k) v[k] = cmul(v[k], tw_dir<DIR>(tws[k * 32 + lane]));
+#pragma unroll
+    for (int k = 0; k < R1; ++k) wr[k * P + lane] = v[k];
     __syncwarp();
   } else {
     // column side: lane (tb, q) of warp w takes t = 2w + tb of pencil q, so the
@@ -236,11 +242,36 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
 #pragma unroll
     for (int i = 0; i < R1; ++i)
       v[i] = (pq < io.valid) ? ld_data(src + (t + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
-    warp_steps12<L, DIR>(v, sm + pq * RG, tws, w32, t);
+    warp_dft<R1, DIR>(v, w32);
+#pragma unroll
+    for (int k = 1; k < R1; ++k) v[k] = cmul(v[k], tw_dir<DIR>(tws[k * 32 + t]));
+    float2* rq = sm + pq * RG;
+#pragma unroll
+    for (int k = 0; k < R1; ++k) rq[k * P + t] = v[k];
     __syncthreads();
   }
   // ---- steps 3 to 5
-  warp_steps345<L, DIR>(v, wr, w32);
+#pragma unroll
+  for (int a = 0; a < R1; ++a) v[a] = wr[k1 * P + C * a + c];
+  warp_dft<R1, DIR>(v, w32);
+#pragma unroll
+  for (int k = 0; k < R1; ++k) {
+    if constexpr (C == 1) {
+      // length 1024: the radix-32 step above was the last level
+    } else if constexpr (C == 2) {
+      v[k] = cmul(v[k], tw_dir<DIR>(w32[c * R1 + k]));  // u_c = W_32^(c k) Z_c
+      const float2 q = make_float2(__shfl_xor_sync(kFull, v[k].x, 1), __shfl_xor_sync(kFull, v[k].y, 1));
+      v[k] = c ? csub(q, v[k]) : cadd(v[k], q);
+    } else {
+      v[k] = cmul(v[k], tw_dir<DIR>(w32[c * R1 + k]));  // u_c = W_32^(c k) Z_c
+      // radix 4 across lanes c = c0 + 2 c1: pairs c1 = 0/1, W_4^(c0 m0), pairs c0 = 0/1
+      float2 q = make_float2(__shfl_xor_sync(kFull, v[k].x, 2), __shfl_xor_sync(kFull, v[k].y, 2));
+      v[k] = (c >> 1) ? csub(q, v[k]) : cadd(v[k], q);
+      if (c == 3) v[k] = mul_w4<DIR>(v[k]);
+      q = make_float2(__shfl_xor_sync(kFull, v[k].x, 1), __shfl_xor_sync(kFull, v[k].y, 1));
+      v[k] = (c & 1) ? csub(q, v[k]) : cadd(v[k], q);
+    }
+  }
   // lane (k1, c) holds X[k1 + R1 k + R1^2 m], k < R1
   if constexpr (KIND == kR2CPost) {
     __syncwarp();  // every lane has read the transpose buffer
