@@ -309,7 +309,8 @@ def main():
                          "split_bf16_1024, split_fp16_tc5_1024, split_bf16_tc5_1024, split_fp32_1024 (C2C "
                          "1024x512x64, staged thread-load launches; tensor-core radix-16 passes unless fp32); "
                          "or pinned_r2c:<fwd bits>:<inv bits> (pinned_slab_r2c: slab plan), dsm_slab_r2c (R2C 512x512x128 slab, "
-                         "plane launches in distributed shared memory), persistent_warp_c2c (C2C 512^3, one persistent "
+                         "plane launches in distributed shared memory), batched_64 / batched_64_staged (the 64 uneven "
+                         "grids, one launch / three stage launches), persistent_warp_c2c (C2C 512^3, one persistent "
                          "launch with warp-per-pencil tile bodies), warp1024_c2c (C2C 1024x512x64, warp-per-pencil "
                          "stages)")
     args = ap.parse_args()
@@ -507,6 +508,22 @@ def ncu_case(name):
     import paper_2601_12209_gb300 as gb
     from paper_2601_12209_gb300 import _build, abi
     _build.build()
+    if name.startswith("batched_64"):
+        # batched_64 / batched_64_staged: the 64 uneven C2C grids (72.4 M points), tuned tile shapes, three forward
+        # transforms as the one launch or as the three stage launches
+        shapes, grids = synth.batched_grids(64, seed=6)
+        m = gb.ManyPlan(shapes)
+        x = m.pack([g.cuda() for g in grids])
+        y = m.empty()
+        # the autotuner's choice on this configuration (tiles per ticket by axis length), set by hand so that
+        # the profiled launches follow few others
+        m.set_tuning(0, {32: 4, 48: 4, 60: 2, 64: 2, 80: 2, 96: 2, 120: 2, 128: 2, 160: 1, 192: 1, 256: 1})
+        torch.cuda.synchronize()
+        run = m.exec_staged if name.endswith("staged") else m.exec
+        for _ in range(3):
+            run(abi.GBFFT_OP_FORWARD, x, y)
+        torch.cuda.synchronize()
+        return
     if name.startswith("split_"):
         # split_<fp16|bf16|fp32>[_tc5]_1024: C2C 1024 x 512 x 64 (268 MB per buffer), x stage has the tensor-core
         # pass (warp-level mma.sync, or tcgen05 with _tc5)
