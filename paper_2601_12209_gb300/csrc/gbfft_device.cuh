@@ -357,7 +357,8 @@ __device__ __forceinline__ void col_store(const float2* sm, const TileIO& io) {
     int p = it & 15, n = it >> 4;
     if (p < io.valid) {
       float2 v = sm[swz(n, p)];
-      st_data(io.gout + p + n * io.out_n, make_float2(v.x * io.scale, v.y * io.scale));
+      if (io.scale != 1.f) v = make_float2(v.x * io.scale, v.y * io.scale);
+      st_data(io.gout + p + n * io.out_n, v);
     }
   }
 }
@@ -1112,11 +1113,13 @@ __device__ __forceinline__ void r2c_post(float2* sm, const float2* tw2, float in
 // straight to global memory, with the roundings of r2c_post then col_store
 // but without the shared-memory write-back and its barrier. Full, aligned
 // tiles move two pencils per 16-byte access (8 lanes per 128-byte line).
-template <int M, int THREADS>
-__device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float2* tw2, float interior,
-                                                   const TileIO& io) {
+// UNIT: interior = scale = 1 (the forward transform), no multiplies.
+template <int M, int THREADS, bool UNIT>
+__device__ __forceinline__ void r2c_post_col_store_impl(const float2* sm, const float2* tw2, float interior,
+                                                        const TileIO& io) {
   constexpr int NPAIR = M / 2 + 1;
   const float sc = io.scale;
+  auto fin = [&](float2 x) { return UNIT ? x : cscale(cscale(x, interior), sc); };
   if (pair_vec_ok(io.gout, io.out_n, io.valid)) {
     for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
       const int p = (it & 7) << 1, k = it >> 3;
@@ -1124,18 +1127,23 @@ __device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float
       const long long rk = (long long)k * (io.out_n >> 1), rm = (long long)(M - k) * (io.out_n >> 1);
       const float4 A = *reinterpret_cast<const float4*>(sm + swz(k, p));
       if (k == 0) {
-        st_data4(g, make_float4((A.x + A.y) * sc, 0.f * sc, (A.z + A.w) * sc, 0.f * sc));
-        st_data4(g + rm, make_float4((A.x - A.y) * sc, 0.f * sc, (A.z - A.w) * sc, 0.f * sc));
+        if (UNIT) {
+          st_data4(g, make_float4(A.x + A.y, 0.f, A.z + A.w, 0.f));
+          st_data4(g + rm, make_float4(A.x - A.y, 0.f, A.z - A.w, 0.f));
+        } else {
+          st_data4(g, make_float4((A.x + A.y) * sc, 0.f * sc, (A.z + A.w) * sc, 0.f * sc));
+          st_data4(g + rm, make_float4((A.x - A.y) * sc, 0.f * sc, (A.z - A.w) * sc, 0.f * sc));
+        }
       } else if (2 * k < M) {
         const float4 B = *reinterpret_cast<const float4*>(sm + swz(M - k, p));
         const float2 w = tw2[k];
         float2 xk0, xm0, xk1, xm1;
         r2c_split_pair(lo2(A), lo2(B), w, xk0, xm0);
         r2c_split_pair(hi2(A), hi2(B), w, xk1, xm1);
-        st_data4(g + rk, cat2(cscale(cscale(xk0, interior), sc), cscale(cscale(xk1, interior), sc)));
-        st_data4(g + rm, cat2(cscale(cscale(xm0, interior), sc), cscale(cscale(xm1, interior), sc)));
+        st_data4(g + rk, cat2(fin(xk0), fin(xk1)));
+        st_data4(g + rm, cat2(fin(xm0), fin(xm1)));
       } else if (2 * k == M) {
-        st_data4(g + rk, cat2(cscale(cscale(cconj(lo2(A)), interior), sc), cscale(cscale(cconj(hi2(A)), interior), sc)));
+        st_data4(g + rk, cat2(fin(cconj(lo2(A))), fin(cconj(hi2(A)))));
       }
     }
     return;
@@ -1146,17 +1154,29 @@ __device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float
     float2* g = io.gout + p;
     if (k == 0) {
       const float2 z0 = sm[swz(0, p)];
-      st_data(g, make_float2((z0.x + z0.y) * sc, 0.f * sc));
-      st_data(g + M * io.out_n, make_float2((z0.x - z0.y) * sc, 0.f * sc));
+      if (UNIT) {
+        st_data(g, make_float2(z0.x + z0.y, 0.f));
+        st_data(g + M * io.out_n, make_float2(z0.x - z0.y, 0.f));
+      } else {
+        st_data(g, make_float2((z0.x + z0.y) * sc, 0.f * sc));
+        st_data(g + M * io.out_n, make_float2((z0.x - z0.y) * sc, 0.f * sc));
+      }
     } else if (2 * k < M) {
       float2 xk, xm;
       r2c_split_pair(sm[swz(k, p)], sm[swz(M - k, p)], tw2[k], xk, xm);
-      st_data(g + k * io.out_n, cscale(cscale(xk, interior), sc));
-      st_data(g + (M - k) * io.out_n, cscale(cscale(xm, interior), sc));
+      st_data(g + k * io.out_n, fin(xk));
+      st_data(g + (M - k) * io.out_n, fin(xm));
     } else if (2 * k == M) {
-      st_data(g + k * io.out_n, cscale(cscale(cconj(sm[swz(k, p)]), interior), sc));
+      st_data(g + k * io.out_n, fin(cconj(sm[swz(k, p)])));
     }
   }
+}
+
+template <int M, int THREADS>
+__device__ __forceinline__ void r2c_post_col_store(const float2* sm, const float2* tw2, float interior,
+                                                   const TileIO& io) {
+  if (interior == 1.f && io.scale == 1.f) r2c_post_col_store_impl<M, THREADS, true>(sm, tw2, interior, io);
+  else r2c_post_col_store_impl<M, THREADS, false>(sm, tw2, interior, io);
 }
 
 // C2R merge (in place, reads rows 0..M, writes rows 0..M-1). Only the real
@@ -1207,7 +1227,8 @@ __device__ __forceinline__ void c2r_load_pair(const TileIO& io, int it, float4& 
   b = ld_data4(g + (long long)(M - k) * (io.in_n >> 1));  // k = 0: row M; 2k = M: row k again
 }
 
-template <int M>
+// UNIT: interior = 1 (the inverse transform), no multiplies.
+template <int M, bool UNIT = false>
 __device__ __forceinline__ void c2r_merge_pair_to(float2* sm, const float2* tw2, float interior, int it, float4 a,
                                                   float4 c) {
   const int p = (it & 7) << 1, k = it >> 3;
@@ -1217,12 +1238,17 @@ __device__ __forceinline__ void c2r_merge_pair_to(float2* sm, const float2* tw2,
   } else if (2 * k < M) {
     const float2 w = tw2[k];
     float2 zk0, zm0, zk1, zm1;
-    c2r_merge_pair(cscale(lo2(a), interior), cscale(lo2(c), interior), w, zk0, zm0);
-    c2r_merge_pair(cscale(hi2(a), interior), cscale(hi2(c), interior), w, zk1, zm1);
+    if (UNIT) {
+      c2r_merge_pair(lo2(a), lo2(c), w, zk0, zm0);
+      c2r_merge_pair(hi2(a), hi2(c), w, zk1, zm1);
+    } else {
+      c2r_merge_pair(cscale(lo2(a), interior), cscale(lo2(c), interior), w, zk0, zm0);
+      c2r_merge_pair(cscale(hi2(a), interior), cscale(hi2(c), interior), w, zk1, zm1);
+    }
     *sk = cat2(zk0, zk1);
     *reinterpret_cast<float4*>(sm + swz(M - k, p)) = cat2(zm0, zm1);
   } else if (2 * k == M) {
-    const float2 x0 = cscale(lo2(a), interior), x1 = cscale(hi2(a), interior);
+    const float2 x0 = UNIT ? lo2(a) : cscale(lo2(a), interior), x1 = UNIT ? hi2(a) : cscale(hi2(a), interior);
     *sk = make_float4(2.f * x0.x, -2.f * x0.y, 2.f * x1.x, -2.f * x1.y);
   }
 }

@@ -59,15 +59,22 @@ __device__ __forceinline__ void c2r_prefetch_issue(float4* raw, const TileIO& io
 }
 
 // Merge the bins held in raw into the tile (same arithmetic as the fused column load).
-template <int M, int THREADS>
-__device__ __forceinline__ void c2r_merge_from_raw(float2* sm, const float4* raw, const float2* tw2, float interior) {
+template <int M, int THREADS, bool UNIT>
+__device__ __forceinline__ void c2r_merge_from_raw_impl(float2* sm, const float4* raw, const float2* tw2,
+                                                        float interior) {
   constexpr int NPAIR = M / 2 + 1;
   for (int it = threadIdx.x; it < NPAIR * 8; it += THREADS) {
     const int k = it >> 3, c = it & 7;
     const float4 a = raw[raw_index(k, c)];
     const float4 b = raw[raw_index(M - k, c)];  // k = 0: row M; 2k = M: row k again
-    c2r_merge_pair_to<M>(sm, tw2, interior, it, a, b);
+    c2r_merge_pair_to<M, UNIT>(sm, tw2, interior, it, a, b);
   }
+}
+
+template <int M, int THREADS>
+__device__ __forceinline__ void c2r_merge_from_raw(float2* sm, const float4* raw, const float2* tw2, float interior) {
+  if (interior == 1.f) c2r_merge_from_raw_impl<M, THREADS, true>(sm, raw, tw2, interior);
+  else c2r_merge_from_raw_impl<M, THREADS, false>(sm, raw, tw2, interior);
 }
 
 // Blocks per SM: the tile and the raw buffer take 2 x 33 KB at M = 256 (three

@@ -76,11 +76,20 @@ __device__ __forceinline__ float2 mul_w4(float2 a) {
 // Column-side store of rows 0..NROWS-1 of the pencil-major tile: lanes run
 // along the 16 pencils of one element (one 128-byte line of global memory).
 // Element n of a pencil sits at n + (n >> PAD_SHIFT) * PAD of its region.
+// An unscaled stage (scale 1, every stage but a transform's last) skips the
+// multiplies.
 template <int NROWS, int RG, int THREADS = kWarpThreads, int PAD_SHIFT = 0, int PAD = 0>
 __device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& io) {
-  for (int it = threadIdx.x; it < NROWS * kTileP; it += THREADS) {
-    const int q = it & 15, n = it >> 4;
-    if (q < io.valid) st_data(io.gout + q + n * io.out_n, cscale(sm[q * RG + n + (n >> PAD_SHIFT) * PAD], io.scale));
+  if (io.scale == 1.f) {
+    for (int it = threadIdx.x; it < NROWS * kTileP; it += THREADS) {
+      const int q = it & 15, n = it >> 4;
+      if (q < io.valid) st_data(io.gout + q + n * io.out_n, sm[q * RG + n + (n >> PAD_SHIFT) * PAD]);
+    }
+  } else {
+    for (int it = threadIdx.x; it < NROWS * kTileP; it += THREADS) {
+      const int q = it & 15, n = it >> 4;
+      if (q < io.valid) st_data(io.gout + q + n * io.out_n, cscale(sm[q * RG + n + (n >> PAD_SHIFT) * PAD], io.scale));
+    }
   }
 }
 
@@ -292,8 +301,12 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
   } else if (row_out) {
     if (p < io.valid) {
       float2* dst = io.gout + row_pencil(d, g0, p, io.out_g);
+      if (io.scale != 1.f) {
 #pragma unroll
-      for (int k = 0; k < R1; ++k) st_data(dst + (k1 + R1 * k + R1 * R1 * m) * io.out_n, cscale(v[k], io.scale));
+        for (int k = 0; k < R1; ++k) v[k] = cscale(v[k], io.scale);
+      }
+#pragma unroll
+      for (int k = 0; k < R1; ++k) st_data(dst + (k1 + R1 * k + R1 * R1 * m) * io.out_n, v[k]);
     }
     if (!row_in) __syncthreads();  // the next column-side tile writes every warp's region
     else __syncwarp();             // this warp's region is reused by the next tile
