@@ -680,9 +680,15 @@ static const WarpKernel* find_warp(const StageDesc& d) {
   if (d.kind == kC2RPre && d.out_mode != kRow) return nullptr;   // the merge writes row-side pairs
   if ((d.kind == kR2CPost || d.kind == kC2RPre) && !d.tw2) return nullptr;
   ensure_registry();
+  // a kernel specialised for the stage's layout, else one for any layout
+  const int io = warp_io(d.in_mode, d.out_mode);
+  const WarpKernel* any = nullptr;
   for (const auto& k : warp_registry())
-    if (k.L == d.L && k.dir == d.dir && k.kind == d.kind) return &k;
-  return nullptr;
+    if (k.L == d.L && k.dir == d.dir && k.kind == d.kind) {
+      if (k.io == io) return &k;
+      if (k.io < 0 && !any) any = &k;
+    }
+  return any;
 }
 
 // Warp-per-pencil launches: when the column side of a stage is linear in

@@ -30,6 +30,7 @@ namespace gbfft {
 
 struct WarpKernel {
   int L, dir, kind;
+  int io;  // warp_io(in_mode, out_mode) the kernel is specialised for, -1 = any
   const void* fn;
   int threads;
   size_t smem;
@@ -47,7 +48,7 @@ constexpr size_t warp_smem_bytes() {
 // length 1024 keeps 32 per lane and its 16 regions take 135 KB: one block.
 __host__ __device__ constexpr int warp_min_blocks(int L) { return L == 256 ? 3 : (L == 1024 ? 1 : 2); }
 
-template <int L, int DIR, int KIND>
+template <int L, int DIR, int KIND, int IO>
 __global__ void __launch_bounds__(kWarpThreads, warp_min_blocks(L)) warp_stage_kernel(StageDesc d) {
   using G = WarpGeom<L>;
   constexpr int RG = G::kRegion;
@@ -63,13 +64,14 @@ __global__ void __launch_bounds__(kWarpThreads, warp_min_blocks(L)) warp_stage_k
     for (int i = threadIdx.x; i <= L; i += kWarpThreads) tw2[i] = d.tw2[i];
   __syncthreads();
   pdl_wait_prev();
-  for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x) warp_tile<L, DIR, KIND>(d, tile, sm, tws, w32, tw2);
+  for (long long tile = blockIdx.x; tile < d.n_tiles; tile += gridDim.x)
+    warp_tile<L, DIR, KIND, IO>(d, tile, sm, tws, w32, tw2);
 }
 
-template <int L, int DIR, int KIND>
+template <int L, int DIR, int KIND, int IO = -1>
 WarpKernel make_warp_entry() {
-  return WarpKernel{L, DIR, KIND, reinterpret_cast<const void*>(&warp_stage_kernel<L, DIR, KIND>), kWarpThreads,
-                    warp_smem_bytes<L>()};
+  return WarpKernel{L, DIR, KIND, IO, reinterpret_cast<const void*>(&warp_stage_kernel<L, DIR, KIND, IO>),
+                    kWarpThreads, warp_smem_bytes<L>()};
 }
 
 // ----------------------------------------------- two-for-one real x stages
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) pair_stage_kernel(StageDesc d
 template <int L2, int DIR>
 WarpKernel make_pair_entry() {
   // registered under the Stockham kind it replaces: length L2 / 2 complex pairs per row
-  return WarpKernel{L2 / 2, DIR, DIR < 0 ? kR2CPost : kC2RPre,
+  return WarpKernel{L2 / 2, DIR, DIR < 0 ? kR2CPost : kC2RPre, -1,
                     reinterpret_cast<const void*>(&pair_stage_kernel<L2, DIR>), kPairThreads,
                     pair_smem_bytes<L2>()};
 }

@@ -77,10 +77,40 @@ __device__ __forceinline__ float2 mul_w4(float2 a) {
 // along the 16 pencils of one element (one 128-byte line of global memory).
 // Element n of a pencil sits at n + (n >> PAD_SHIFT) * PAD of its region.
 // An unscaled stage (scale 1, every stage but a transform's last) skips the
-// multiplies.
-template <int NROWS, int RG, int THREADS = kWarpThreads, int PAD_SHIFT = 0, int PAD = 0>
+// multiplies. FIXED (the rows -> columns launches): thread (q, n0) stores rows
+// n0 + i (THREADS / 16) in whole passes (compile-time shared-memory offsets,
+// one pointer step per row), then the rows left.
+template <int NROWS, int RG, int THREADS = kWarpThreads, int PAD_SHIFT = 0, int PAD = 0, bool FIXED = false>
 __device__ __forceinline__ void warp_col_store(const float2* sm, const TileIO& io) {
-  if (io.scale == 1.f) {
+  if constexpr (FIXED) {
+    constexpr int RPP = THREADS / kTileP;  // rows per pass
+    constexpr int PASSES = NROWS / RPP;
+    static_assert(PAD == 0 || (1 << PAD_SHIFT) % RPP == 0, "a pass stays inside one padded block");
+    const int q = threadIdx.x & 15, n0 = threadIdx.x / kTileP;
+    if (q < io.valid) {
+      const float2* src = sm + q * RG + n0;
+      float2* dst = io.gout + q + (long long)n0 * io.out_n;
+      const long long step = (long long)RPP * io.out_n;
+      if (io.scale == 1.f) {
+#pragma unroll
+        for (int i = 0; i < PASSES; ++i) {
+          st_data(dst, src[i * RPP + ((i * RPP) >> PAD_SHIFT) * PAD]);
+          dst += step;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < PASSES; ++i) {
+          st_data(dst, cscale(src[i * RPP + ((i * RPP) >> PAD_SHIFT) * PAD], io.scale));
+          dst += step;
+        }
+      }
+    }
+    for (int it = PASSES * RPP * kTileP + threadIdx.x; it < NROWS * kTileP; it += THREADS) {
+      const int qq = it & 15, n = it >> 4;
+      if (qq < io.valid)
+        st_data(io.gout + qq + n * io.out_n, cscale(sm[qq * RG + n + (n >> PAD_SHIFT) * PAD], io.scale));
+    }
+  } else if (io.scale == 1.f) {
     for (int it = threadIdx.x; it < NROWS * kTileP; it += THREADS) {
       const int q = it & 15, n = it >> 4;
       if (q < io.valid) st_data(io.gout + q + n * io.out_n, sm[q * RG + n + (n >> PAD_SHIFT) * PAD]);
@@ -195,7 +225,12 @@ __device__ __forceinline__ void warp_steps345(float2 (&v)[WarpGeom<L>::R1], cons
 // twiddles), tw2 = W_2L^k (real kinds); all in shared memory. Called by
 // all kWarpThreads threads of the block; the tile's region and twiddles are
 // the caller's.
-template <int L, int DIR, int KIND>
+// Layout of a warp-per-pencil launch: IO = 2 in_mode + out_mode (kRow 0, kCol 1)
+// fixes the two sides at compile time, so a kernel holds only its own load and
+// store paths; IO = -1 reads them from the descriptor (the persistent kernel).
+__host__ __device__ constexpr int warp_io(int in_mode, int out_mode) { return 2 * in_mode + out_mode; }
+
+template <int L, int DIR, int KIND, int IO = -1>
 __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, float2* sm, const float2* tws,
                                           const float2* w32, const float2* tw2) {
   using G = WarpGeom<L>;
@@ -205,7 +240,8 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
   const int k1 = lane / C, c = lane % C;
   const int m = C == 2 ? c : ((c >> 1) + 2 * (c & 1));  // output block of this lane after step 5
   float2* wr = sm + p * RG;                               // this warp's pencil region
-  const bool row_in = d.in_mode == kRow, row_out = d.out_mode == kRow;
+  const bool row_in = IO < 0 ? d.in_mode == kRow : (IO >> 1) == kRow;
+  const bool row_out = IO < 0 ? d.out_mode == kRow : (IO & 1) == kRow;
   int o, g0;
   const TileIO io = make_io(d, tile, o, g0);
   float2 v[R1];
@@ -231,11 +267,18 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
       for (int i = 0; i < R1; ++i) v[i] = wr[lane + 32 * i];
       __syncwarp();  // the transpose buffer overwrites the pencil
     } else {
-      // lane t of warp p: x[t + 32 i] of pencil p (coalesced along the row)
+      // lane t of warp p: x[t + 32 i] of pencil p (coalesced along the row; a row side has element
+      // stride 1, which the rows -> columns launches spell out as immediate offsets)
       const float2* src = io.gin + row_pencil(d, g0, p, io.in_g);
+      if (IO == warp_io(kRow, kCol) && io.in_n == 1) {
+        src += lane;
 #pragma unroll
-      for (int i = 0; i < R1; ++i)
-        v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
+        for (int i = 0; i < R1; ++i) v[i] = (p < io.valid) ? ld_data(src + 32 * i) : make_float2(0.f, 0.f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < R1; ++i)
+          v[i] = (p < io.valid) ? ld_data(src + (lane + 32 * i) * io.in_n) : make_float2(0.f, 0.f);
+      }
     }
     warp_dft<R1, DIR>(v, w32);
 #pragma unroll
@@ -320,7 +363,7 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
 #pragma unroll
     for (int k = 0; k < R1; ++k) wr[k1 + R1 * k + R1 * R1 * m + m * kPad] = v[k];
     __syncthreads();
-    warp_col_store<L, RG, kWarpThreads, kPadShift, kPad>(sm, io);
+    warp_col_store<L, RG, kWarpThreads, kPadShift, kPad, IO == warp_io(kRow, kCol)>(sm, io);
     __syncthreads();
   }
 }
