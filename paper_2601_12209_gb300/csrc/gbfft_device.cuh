@@ -325,10 +325,27 @@ __device__ __forceinline__ void row_load(float2* sm, const TileIO& io) {
   }
 }
 
-template <int THREADS, int NROWS>
+// FIXED (a team of one thread per row, NROWS == THREADS): thread n stores the
+// 8 pencil pairs of row n with one pointer step per pair.
+template <int THREADS, int NROWS, bool FIXED = false>
 __device__ __forceinline__ void row_store(const float2* sm, const TileIO& io) {
   const float sc = io.scale;
   const bool unit = sc == 1.f;
+  if constexpr (FIXED) {
+    static_assert(NROWS == THREADS, "one thread per row");
+    const int n = ttid<THREADS>();
+    float2* g = io.gout + n;
+    const long long step = 2 * io.out_g;
+#pragma unroll
+    for (int pair = 0; pair < 8; ++pair) {
+      float4 v = *reinterpret_cast<const float4*>(sm + ((n << 4) | ((pair ^ (n & 7)) << 1)));
+      if (!unit) v = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
+      if (2 * pair < io.valid) st_data(g, make_float2(v.x, v.y));
+      if (2 * pair + 1 < io.valid) st_data(g + io.out_g, make_float2(v.z, v.w));
+      g += step;
+    }
+    return;
+  }
   for (int it = ttid<THREADS>(); it < NROWS * 8; it += THREADS) {
     int n = it % NROWS, pair = it / NROWS;
     int p0 = 2 * pair;

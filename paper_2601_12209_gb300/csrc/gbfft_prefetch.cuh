@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(threads_for(M), prefetch_min_blocks(M)) c2r_pr
       if (pair_vec_ok(nio.gin, nio.in_n, nio.valid)) c2r_prefetch_issue<M, THREADS>(raw, nio);
     }
     fft_passes<M, +1, THREADS, false, false, false>(sm, tw, io);
-    row_store<THREADS, M>(sm, io);
+    row_store<THREADS, M, THREADS == M>(sm, io);
     __syncthreads();
   }
   cp_async_wait_all();
