@@ -363,7 +363,7 @@ __device__ __forceinline__ void warp_tile(const StageDesc& d, long long tile, fl
 #pragma unroll
     for (int k = 0; k < R1; ++k) wr[k1 + R1 * k + R1 * R1 * m + m * kPad] = v[k];
     __syncthreads();
-    warp_col_store<L, RG, kWarpThreads, kPadShift, kPad, IO == warp_io(kRow, kCol)>(sm, io);
+    warp_col_store<L, RG, kWarpThreads, kPadShift, kPad, IO >= 0 && (IO & 1) == kCol>(sm, io);
     __syncthreads();
   }
 }

@@ -12,6 +12,8 @@ void register_warp_group_0(std::vector<WarpKernel>& v) {
   v.push_back(make_warp_entry<512, 1, kPlain>());
   v.push_back(make_warp_entry<512, -1, kPlain, warp_io(kRow, kCol)>());
   v.push_back(make_warp_entry<512, 1, kPlain, warp_io(kRow, kCol)>());
+  v.push_back(make_warp_entry<512, -1, kPlain, warp_io(kCol, kCol)>());
+  v.push_back(make_warp_entry<512, 1, kPlain, warp_io(kCol, kCol)>());
   v.push_back(make_warp_entry<256, -1, kPlain>());
   v.push_back(make_warp_entry<256, 1, kPlain>());
   // the real x stages of 512-point rows: two rows per length-512 complex FFT
