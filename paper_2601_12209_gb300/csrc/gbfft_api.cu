@@ -1050,6 +1050,27 @@ static unsigned persistent_warp_mask(const Pipeline& P, const PersistentKernel* 
 }
 
 // warp_mask bit s: stage s runs the warp-per-pencil tile body (where it can).
+// Write-after-read / write-after-write ordering inside one launch. The
+// dependency rules order each tile after the producer tiles it reads, not
+// after the tiles of earlier stages that read or wrote the buffer it
+// overwrites (a pencil pipeline's last stage writes the output buffer that the
+// middle stage reads and the first stage wrote). Stage s therefore waits for
+// the whole of the latest earlier stage r that touched its output buffer,
+// except the previous stage writing it for an in-place stage s (then s reads
+// exactly what its producers wrote). The completion of stage r implies that of
+// every stage before it: each tile of a stage is read by some tile of the next.
+static void persistent_war(const Pipeline& P, int* war) {
+  for (int s = 0; s < kMaxStages; ++s) war[s] = -1;
+  for (int s = 1; s < P.n; ++s) {
+    const void* o = P.st[s].out;
+    for (int r = 0; r < s; ++r) {
+      const bool reads = P.st[r].in == o, writes = P.st[r].out == o;
+      if (r == s - 1 && !reads) continue;  // the producer writing what s reads (or nothing of o)
+      if (reads || writes) war[s] = r;
+    }
+  }
+}
+
 static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKernel* pk, cudaStream_t stream,
                           unsigned warp_mask, int tiles_per_ticket) {
   PersistentArgs a;
@@ -1085,6 +1106,7 @@ static int run_persistent(gbfft_plan_s* p, const Pipeline& P, const PersistentKe
   a.timeout_ns = dbg ? 20000000LL : 2000000000LL;
   a.debug_never = dbg ? 1 : 0;
   for (int s = 0; s < P.n; ++s) a.sig[s] = s + 1 < P.n ? persistent_sig_for_rule(P.st[s + 1].dep_rule) : 0;
+  persistent_war(P, a.war);
   cudaError_t e = cudaMemsetAsync(&p->ctl->ticket, 0, 2 * sizeof(unsigned int) + p->counters_words * sizeof(unsigned int),
                                   stream);
   if (e != cudaSuccess) return GBFFT_ERR_CUDA;
@@ -2133,6 +2155,14 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, int kind, int
         words += 1;
         sg.p_outer = sg.p_outer16 = sg.p_gchunk = sg.p_total = sg.p_stage = -1;
         sg.prev_tiles = 0;
+        sg.w_stage = -1;
+        sg.w_tiles = 0;
+        if (k == 2) {
+          // the last stage writes `out`, which the middle stage (same grid) reads
+          const ManySegment& r = segs[(size_t)count + g];
+          sg.w_stage = r.c_stage;
+          sg.w_tiles = r.d.n_tiles;
+        }
         if (k > 0) {
           const ManySegment& q = segs[(size_t)(k - 1) * count + g];
           sg.p_outer = q.c_outer;

@@ -176,6 +176,10 @@ struct PersistentArgs {
   // consecutive tiles of one stage per ticket (1, 2 or 4): the ticket, the
   // dependency look-ahead and the publishing fence are paid once per ticket
   int tiles_per_ticket;
+  // war[s] >= 0: stage s writes a buffer that stage war[s] (< s) read or wrote,
+  // so its tiles first wait for that whole stage (write-after-read / -write:
+  // the dependency rules order only the producer tiles a tile reads); -1: none
+  int war[kMaxStages];
 };
 
 constexpr int kMaxTicketTiles = 4;
@@ -266,9 +270,16 @@ __device__ __forceinline__ const unsigned int* dep_counter(const PersistentArgs&
 __device__ __forceinline__ bool wait_deps(const PersistentArgs& a, const StageDesc* st, int* complete, int s,
                                           long long tile) {
   if (s == 0) return true;
+  const unsigned int extra = a.debug_never ? 1u : 0u;
+  const int w = a.war[s];
+  if (w >= 0 && !complete[w]) {
+    // the whole earlier stage that touched this stage's output buffer
+    if (!wait_counter(a.cnt_stage[w], (unsigned int)st[w].n_tiles + extra, a.ctl, a.timeout_ns, global_ns()))
+      return false;
+    complete[w] = 1;
+  }
   const StageDesc& d = st[s];
   if (d.dep_rule == kDepNone || complete[s - 1]) return true;
-  const unsigned int extra = a.debug_never ? 1u : 0u;
   if (ld_acquire(a.cnt_stage[s - 1]) >= (unsigned int)st[s - 1].n_tiles + extra) {
     complete[s - 1] = 1;
     return true;
@@ -502,10 +513,16 @@ persistent_kernel(PersistentArgs a) {
               any = true;
             }
           }
+        // the whole earlier stage whose buffer the next ticket's stage overwrites
+        const int w = s1 > 0 ? a.war[s1] : -1;
+        const bool wchk = w >= 0 && !s_complete[w];
+        const unsigned int wv = wchk ? ld_relaxed(a.cnt_stage[w]) : 0u;
+        any = any || wchk;
         if (any) asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the loads above, then the tiles
 #pragma unroll
         for (int j = 0; j < kMaxTicketTiles; ++j)
           if (lp[j] && lv[j] < lt[j]) go = 0;
+        if (wchk && wv < (unsigned int)s_st[w].n_tiles + (a.debug_never ? 1u : 0u)) go = 0;
       }
       t2 = atomicAdd(&a.ctl->ticket, 1u);  // needed one ticket later
       s_tk[slot ^ 1] = t1;

@@ -39,6 +39,9 @@ struct ManySegment {
   // counters of the producer segment (same grid, previous stage); -1 if none
   long long p_outer, p_outer16, p_gchunk, p_total, p_stage;
   long long prev_tiles;  // tiles of the producer segment
+  // stage counter and tile count of the segment (same grid) that read the buffer this segment
+  // overwrites (one launch: the last stage writes the output buffer the middle stage reads); -1 if none
+  long long w_stage, w_tiles;
 };
 
 struct ManyArgs {
@@ -133,8 +136,15 @@ __device__ __forceinline__ bool many_wait_tile(const ManyArgs& a, const ManySegm
   }
 }
 
-// Waits for the producer tiles of every tile of ticket t0.
+// Waits for the producer tiles of every tile of ticket t0, after the whole
+// segment that read the buffer this one overwrites (write-after-read: the
+// dependency rules order only the tiles a tile reads).
 __device__ __forceinline__ bool many_wait(const ManyArgs& a, const ManySegment& m, long long t0) {
+  if (m.w_stage >= 0) {
+    const unsigned int extra = a.debug_never ? 1u : 0u;
+    if (!wait_counter(a.counters + m.w_stage, (unsigned int)m.w_tiles + extra, a.ctl, a.timeout_ns, global_ns()))
+      return false;
+  }
   for (int j = 0; j < m.teams; ++j) {
     const long long tile = t0 * m.teams + j;
     if (tile >= m.d.n_tiles) break;

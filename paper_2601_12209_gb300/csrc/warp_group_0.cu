@@ -1,5 +1,6 @@
 // Warp-per-pencil stage kernels: complex lengths 512 (any layout, and specialised
-// for rows -> columns) and 256, forward and inverse; and the
+// for rows -> columns and columns -> columns) and 256 (any layout, and rows ->
+// columns), forward and inverse; and the
 // real x stages of 512-point rows (R2C, C2R) as two-for-one length-512 complex
 // transforms.
 #include "gbfft_warp.cuh"
@@ -16,6 +17,8 @@ void register_warp_group_0(std::vector<WarpKernel>& v) {
   v.push_back(make_warp_entry<512, 1, kPlain, warp_io(kCol, kCol)>());
   v.push_back(make_warp_entry<256, -1, kPlain>());
   v.push_back(make_warp_entry<256, 1, kPlain>());
+  v.push_back(make_warp_entry<256, -1, kPlain, warp_io(kRow, kCol)>());
+  v.push_back(make_warp_entry<256, 1, kPlain, warp_io(kRow, kCol)>());
   // the real x stages of 512-point rows: two rows per length-512 complex FFT
   v.push_back(make_pair_entry<512, -1>());
   v.push_back(make_pair_entry<512, 1>());

@@ -190,3 +190,38 @@ def test_persistent_tiles_per_ticket_bitwise(gb, kind):
     assert oracle.rel_l2(outs[0][1].cpu().numpy(), x.numpy()) < TOL
     with pytest.raises(abi.GbfftError):
         abi.gbfft_plan_set_tuning(p.handle, 0, True, 3 << 25)  # 8 tiles per ticket: not built
+
+
+@pytest.mark.parametrize("kind", ["c2c", "r2c"])
+def test_persistent_repeated_equals_staged(gb, kind):
+    """Repeated one-launch transforms against the stage launches, bit for bit. The last stage of a pencil
+    pipeline overwrites the buffer its middle stage reads (and the Poisson pipeline's inverse y stage the
+    forward y stage's input), so inside one launch it must wait for that whole stage; a tile that ran ahead
+    would corrupt data another tile had not yet read. 60 launches per tile-per-ticket choice."""
+    from paper_2601_12209_gb300 import abi
+    n = 64
+    x = (synth.normal_real((2, n, n, n), seed=98) if kind == "r2c" else synth.uniform_complex((2, n, n, n), seed=98))
+    xd = x.cuda()
+    ref = gb.Plan(n, n, n, kind=kind, batch=2, staged=True)
+    y0 = ref.forward(xd)
+    z0 = ref.inverse(y0)
+    p = gb.Plan(n, n, n, kind=kind, batch=2)
+    pipes = (0, 1, 2) if kind == "r2c" else (0, 1)
+    ph0 = None
+    if kind == "r2c":
+        rp = gb.Plan(n, n, n, kind=kind, staged=True)
+        pq = gb.Plan(n, n, n, kind=kind)
+        ph0 = rp.poisson(xd[0])
+    for log_t in (0, 2):
+        for pipe in pipes:
+            abi.gbfft_plan_set_tuning(p.handle, pipe, True, log_t << 25)
+        if kind == "r2c":
+            abi.gbfft_plan_set_tuning(pq.handle, 2, True, log_t << 25)
+        for _ in range(60):
+            y = p.forward(xd)
+            z = p.inverse(y)
+            assert torch.equal(y, y0) and torch.equal(z, z0)
+            if kind == "r2c":
+                assert torch.equal(pq.poisson(xd[0]), ph0)
+    torch.cuda.synchronize()
+    assert p.device_error() == 0
