@@ -354,8 +354,9 @@ int gbfft_exec_c2c_noalloc(int nx, int ny, int nz, int op, const void* in, void*
  * every grid from one ticket counter (bounded per-grid dependency waits). The
  * grids are packed back to back in `in` and `out` (grid g starts at element
  * offset gbfft_many_layout(g); every grid starts 16-byte aligned). The launch
- * needs only in/out and plan-owned memory, so it can be captured in a CUDA
- * graph and replayed. count <= 85.
+ * needs only in/out and plan-owned memory (two workspaces of the packed size,
+ * so that no stage overwrites what an earlier stage of its grid reads), so it
+ * can be captured in a CUDA graph and replayed. count <= 85.
  *   kind, dtype : as in gbfft_plan_create; batching is built for GBFFT_C2C with
  *                 GBFFT_FP32 only (any other combination: GBFFT_ERR_INVALID_ARG)
  *   flags       : 0 or GBFFT_DEBUG_TIMEOUT
@@ -389,7 +390,7 @@ int gbfft_many_autotune(gbfft_many m, void* stream);
 int gbfft_many_get_tuning(gbfft_many m, int pipeline, int* lengths, int* teams, int cap, int* n, float* ms);
 /* Set tiles per ticket by hand (teams 1, 2 or 4, at most what the length allows; synchronous upload). */
 int gbfft_many_set_tuning(gbfft_many m, int pipeline, const int* lengths, const int* teams, int n);
-/* Queue lag of the one launch (chosen by gbfft_many_autotune from 1, 2, 4): stage s of grid g is queued at
+/* Queue lag of the one launch (chosen by gbfft_many_autotune from 1, 2, 4, 8): stage s of grid g is queued at
    slot g + s * lag, so a larger lag queues a grid's next stage further behind its producer. Every dependency
    keeps a smaller ticket for any lag. set: 1..8 (synchronous upload; not during stream capture). */
 int gbfft_many_get_lag(gbfft_many m, int pipeline, int* lag);

@@ -1997,6 +1997,7 @@ struct gbfft_many_s {
   int nseg = 0;
   const ManyKernel* kern[2] = {nullptr, nullptr};
   void* ws = nullptr;
+  void* ws2 = nullptr;
   Control* ctl = nullptr;
   unsigned int* counters = nullptr;
   size_t counter_words = 0;
@@ -2014,6 +2015,7 @@ static void free_many(gbfft_many_s* m) {
     cudaFree(m->tile_seg_q[i]);
   }
   cudaFree(m->ws);
+  cudaFree(m->ws2);
   cudaFree(m->ctl);
   delete m;
 }
@@ -2128,7 +2130,10 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, int kind, int
       }
       P[g] = build_pipeline(m->plans[g], pipe, op, none, none, none, none);
     }
-    const int roles[3][2] = {{0, 1}, {1, 2}, {2, 1}};  // C2C pencil: in->out, out->ws, ws->out
+    // in -> ws, ws -> ws2, ws2 -> out: no stage of a grid overwrites a buffer an earlier stage of the grid
+    // read or wrote, so the one launch needs no ordering beyond each tile's producers (with out as the
+    // middle buffer, the last stage would overwrite it while middle-stage tiles still read it)
+    const int roles[3][2] = {{0, 2}, {2, 3}, {3, 1}};
     std::vector<ManySegment>& segs = m->base[pipe];
     unsigned int acc = 0;
     for (int k = 0; k < 3; ++k)
@@ -2155,14 +2160,6 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, int kind, int
         words += 1;
         sg.p_outer = sg.p_outer16 = sg.p_gchunk = sg.p_total = sg.p_stage = -1;
         sg.prev_tiles = 0;
-        sg.w_stage = -1;
-        sg.w_tiles = 0;
-        if (k == 2) {
-          // the last stage writes `out`, which the middle stage (same grid) reads
-          const ManySegment& r = segs[(size_t)count + g];
-          sg.w_stage = r.c_stage;
-          sg.w_tiles = r.d.n_tiles;
-        }
         if (k > 0) {
           const ManySegment& q = segs[(size_t)(k - 1) * count + g];
           sg.p_outer = q.c_outer;
@@ -2197,6 +2194,7 @@ int gbfft_many_create(gbfft_many* out, int count, const int* dims, int kind, int
   }
   void* c = nullptr;
   ok = ok && cudaMalloc(&m->ws, (size_t)m->total * sizeof(float2)) == cudaSuccess &&
+       cudaMalloc(&m->ws2, (size_t)m->total * sizeof(float2)) == cudaSuccess &&
        cudaMalloc(&c, sizeof(Control) + m->counter_words * sizeof(unsigned int)) == cudaSuccess &&
        cudaMemset(c, 0, sizeof(Control) + m->counter_words * sizeof(unsigned int)) == cudaSuccess;
   if (!ok) {
@@ -2244,6 +2242,7 @@ static int many_launch(gbfft_many m, int op, const void* in, void* out, void* st
   a.in = reinterpret_cast<const float2*>(in);
   a.out = reinterpret_cast<float2*>(out);
   a.ws = reinterpret_cast<float2*>(m->ws);
+  a.ws2 = reinterpret_cast<float2*>(m->ws2);
   a.ctl = m->ctl;
   a.counters = m->counters;
   const bool dbg = (m->flags & GBFFT_DEBUG_TIMEOUT) != 0;
@@ -2360,7 +2359,7 @@ int gbfft_many_autotune(gbfft_many m, void* stream) {
         m->teams_by_len[pipe][L] = best_s;
       }
     // queue lag between a grid's stages
-    for (int lag : {2, 4}) {
+    for (int lag : {2, 4, 8}) {
       if (rc) break;
       const int keep = m->lag[pipe];
       m->lag[pipe] = lag;

@@ -29,7 +29,7 @@ namespace gbfft {
 // base[in_buf] + in_off and base[out_buf] + out_off.
 struct ManySegment {
   StageDesc d;
-  int in_buf, out_buf;  // 0 in, 1 out, 2 workspace
+  int in_buf, out_buf;  // 0 in, 1 out, 2 and 3 the two workspaces
   // counters the consumer segment reads (kSig* bits); the others are not written
   int sig_mask;
   int teams;  // S: tiles per ticket (1, 2 or 4), one team of kManyThreads / S threads each
@@ -39,9 +39,6 @@ struct ManySegment {
   // counters of the producer segment (same grid, previous stage); -1 if none
   long long p_outer, p_outer16, p_gchunk, p_total, p_stage;
   long long prev_tiles;  // tiles of the producer segment
-  // stage counter and tile count of the segment (same grid) that read the buffer this segment
-  // overwrites (one launch: the last stage writes the output buffer the middle stage reads); -1 if none
-  long long w_stage, w_tiles;
 };
 
 struct ManyArgs {
@@ -53,6 +50,7 @@ struct ManyArgs {
   const float2* in;
   float2* out;
   float2* ws;
+  float2* ws2;
   Control* ctl;
   unsigned int* counters;
   long long timeout_ns;
@@ -136,15 +134,11 @@ __device__ __forceinline__ bool many_wait_tile(const ManyArgs& a, const ManySegm
   }
 }
 
-// Waits for the producer tiles of every tile of ticket t0, after the whole
-// segment that read the buffer this one overwrites (write-after-read: the
-// dependency rules order only the tiles a tile reads).
+// Waits for the producer tiles of every tile of ticket t0. (The stages of a
+// grid write three distinct buffers, ws, ws2 and out, so no stage overwrites
+// what an earlier stage read or wrote: the producer tiles are the only order
+// a tile needs.)
 __device__ __forceinline__ bool many_wait(const ManyArgs& a, const ManySegment& m, long long t0) {
-  if (m.w_stage >= 0) {
-    const unsigned int extra = a.debug_never ? 1u : 0u;
-    if (!wait_counter(a.counters + m.w_stage, (unsigned int)m.w_tiles + extra, a.ctl, a.timeout_ns, global_ns()))
-      return false;
-  }
   for (int j = 0; j < m.teams; ++j) {
     const long long tile = t0 * m.teams + j;
     if (tile >= m.d.n_tiles) break;
@@ -212,8 +206,8 @@ __global__ void __launch_bounds__(kManyThreads, 3) many_kernel(ManyArgs a) {
     for (int i = threadIdx.x; i < (int)(sizeof(ManySegment) / 8); i += 32) dst[i] = src[i];
     __syncwarp();
     if (threadIdx.x == 0) {
-      const float2* bases_in[3] = {a.in, a.out, a.ws};
-      float2* bases_out[3] = {const_cast<float2*>(a.in), a.out, a.ws};
+      const float2* bases_in[4] = {a.in, a.out, a.ws, a.ws2};
+      float2* bases_out[4] = {const_cast<float2*>(a.in), a.out, a.ws, a.ws2};
       s_seg.d.in = bases_in[s_seg.in_buf] + s_seg.in_off;
       s_seg.d.out = bases_out[s_seg.out_buf] + s_seg.out_off;
       s_tile = (long long)(t - a.first[seg]);
